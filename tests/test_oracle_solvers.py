@@ -1,0 +1,64 @@
+"""Pins for oracle.solvers: GMRES against dense LU, restarts, breakdown, caps."""
+import numpy as np
+import pytest
+
+from oracle import mesh as M, operator as OP, solvers as SO
+
+
+def _system(d=1, nel=(6, 3, 2), nt=5, bc=M.PERIODIC, seed=1):
+    rng = np.random.default_rng(seed)
+    me = M.Mesh(d, [nel[0], nel[1], nel[2], nt], [0, 0, 0, 0], [1.0, 1.0, 1.0, 0.5], [bc] * 3)
+    psi0 = rng.standard_normal(me.spatial_shape) + 1j * rng.standard_normal(me.spatial_shape)
+    V = rng.uniform(0, 1, me.nel[0] * me.nel[1] * me.nel[2])
+    A22, b = OP.split(me, OP.assemble(me, 1.0, V), psi0)
+    return me, A22, b
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_full_gmres_equals_lu(d):
+    me, A, b = _system(d=d, nel=(4, 3, 2), nt=3)
+    n = b.size
+    x_lu = SO.dense_solve(A, b)
+    r = SO.gmres(lambda v: A @ v, b, restart=n, rtol=1e-13, maxiter=n)
+    assert r.converged
+    assert np.linalg.norm(r.x - x_lu) / np.linalg.norm(x_lu) < 1e-11
+
+
+def test_restarted_gmres_equals_lu():
+    me, A, b = _system(d=1, nel=(16, 1, 1), nt=12)
+    x_lu = SO.dense_solve(A, b)
+    r = SO.gmres(lambda v: A @ v, b, restart=10, rtol=1e-13, maxiter=20000)
+    assert r.converged and r.restarts > 1
+    assert np.linalg.norm(r.x - x_lu) / np.linalg.norm(x_lu) < 1e-10
+    assert r.rel_resid_true <= 1e-13
+    assert abs(r.history[-1] - r.rel_resid_true) < 1e-12
+
+
+def test_gmres_lucky_breakdown():
+    # b in a 3-dimensional invariant subspace: exact solution after 3 steps
+    A = np.diag([1.0, 2.0, 3.0, 4.0, 5.0]).astype(complex)
+    b = np.array([1.0, 1.0, 1.0, 0, 0], dtype=complex)
+    r = SO.gmres(lambda v: A @ v, b, restart=5, rtol=1e-15)
+    assert r.breakdown and r.iters == 3
+    assert np.allclose(r.x, [1, 0.5, 1 / 3, 0, 0])
+
+
+def test_gmres_maxiter_reports_not_converged():
+    me, A, b = _system(d=1, nel=(16, 1, 1), nt=12)
+    r = SO.gmres(lambda v: A @ v, b, restart=5, rtol=1e-14, maxiter=7)
+    assert not r.converged and r.iters == 7
+    # history is non-increasing within a cycle (GMRES minimises the residual)
+    h = r.history[:5]
+    assert all(h[i + 1] <= h[i] + 1e-15 for i in range(len(h) - 1))
+
+
+def test_gmres_zero_rhs():
+    r = SO.gmres(lambda v: v, np.zeros(4, dtype=complex))
+    assert r.converged and r.iters == 0 and np.all(r.x == 0)
+
+
+def test_givens_zeroes_second_entry():
+    for a, b in [(1 + 2j, 0.5), (0, 2.0), (3 - 1j, 0.0), (1e-300 + 0j, 1.0)]:
+        c, s = SO.givens(a, b)
+        assert abs(-np.conj(s) * a + c * b) < 1e-15 * max(abs(a), abs(b), 1)
+        assert abs(c * c + abs(s) ** 2 - 1) < 1e-15
