@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-solution of the spacetime FEM Dirac solve on GB300.
+
+One step = one whole solve of the 2+1 Zitterbewegung workload (96 x 96 space
+x 96 time Q1 elements, 2-component spinor, 1,769,472 complex unknowns) to
+relative residual 1e-8: right-hand side, FP32 operator applies inside GMRES(30),
+FP64 CGS2 orthogonalisation, Givens/least squares, FP64 iterative refinement.
+Inputs are resident in HBM when the timed region starts; the GMRES basis
+(31 x 28 MB) exceeds L2, so no L2 flush is needed between steps.
+
+Also reported on the same line: the plain-FP64-GMRES time-to-solution of the
+same system, the standalone operator-apply bandwidth (rotating buffers > 2x L2),
+the roofline of the dominant kernel class measured with CUDA events inside the
+timed solves, the end-to-end time through the C ABI with host buffers, and the
+FP64 CPU oracle timed on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 runs under torch.distributed.run: independent replicas, one per GPU.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+RTOL = 1e-8
+RESTART = 30
+INNER_RTOL = 1e-4
+HBM_FALLBACK_GBS = 6800.0
+SMS = 152
+SM_MAX_MHZ = 2070.0
+FP64_FLOP_PER_CLK_SM = 4.0     # 2 FP64 FMA per clock per SM (1/64 of the FP32 rate)
+FP32_FLOP_PER_CLK_SM = 256.0   # 128 FP32 FMA per clock per SM
+CLASSES = ("apply64", "apply32", "cast", "project", "update", "scale", "misc", "rhs")
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", HBM_FALLBACK_GBS), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def iteration_count(name):
+    p = os.path.join(ROOT, "tests", "golden", "oracle_iteration_counts.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if name in d and d[name].get("converged"):
+            return d[name]["iters"]
+    return None
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_seconds_per_step(w, k=4):
+    """Seconds per Arnoldi step of the oracle's GMRES(30), as it stands, on the full mesh.
+
+    Difference of two oracle solves capped at 1 and 1 + k steps (both include
+    the same initial and final residual applies), divided by k.
+    """
+    from oracle import mesh as OM, operator as OOP, solvers as OS
+    om = OM.Mesh(w.d, w.n_el, w.lo, w.hi, w.bc)
+    b = OOP.rhs(om, w.m, w.V, w.psi0)
+    A = lambda v: OOP.apply(om, w.m, w.V, v)  # noqa: E731
+    t0 = time.perf_counter()
+    OS.gmres(A, b, restart=RESTART, rtol=RTOL, maxiter=1)
+    t1 = time.perf_counter()
+    OS.gmres(A, b, restart=RESTART, rtol=RTOL, maxiter=1 + k)
+    t2 = time.perf_counter()
+    return max((t2 - t1) - (t1 - t0), 1e-9) / k
+
+
+def host_cores():
+    return os.cpu_count() or 1
+
+
+def run_reference(args, rank):
+    """The FP64 CPU oracle on the host cores, same workload / metric / unit."""
+    if rank != 0:
+        return
+    w = W.zb_2p1()
+    n_iter = iteration_count("zb_2p1")
+    k = 2
+    for _ in range(args.warmup):
+        oracle_seconds_per_step(w, k)
+    per = [oracle_seconds_per_step(w, k) for _ in range(args.steps)]
+    sec_step = statistics.mean(per)
+    if n_iter is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle GMRES step count for zb_2p1 not recorded "
+                          "(run python -m oracle.iteration_counts)"}))
+        return
+    solve_s = sec_step * n_iter
+    value = 1.0 / solve_s
+    sample = ("each step: the oracle's GMRES(%d) from x0 = 0 on the full 96x96x96 system for 1 and %d Arnoldi "
+              "steps; the difference / %d is the seconds per step, times the oracle's own %d-step solve "
+              "(rel. resid %g) recorded by oracle/iteration_counts.py" % (RESTART, 1 + k, k, n_iter, RTOL))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * solve_s,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": host_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- GPU arm
+
+METRIC = "operator-apply HBM GB/s; time-to-solution at rel. resid 1e-8 vs plain FP64 GMRES"
+CONFIG = {"workload": "zb_2p1: 2+1 Zitterbewegung packet (sigma 0.5, p0 (2,0), seed 20210326), Q1 mesh "
+                      "96x96 space x 96 time on [-8,8]^2 x [0,4], periodic, m = 1, NC = 2, 1769472 complex "
+                      "unknowns; GMRES(30) with FP32 operator apply inside FP64 iterative refinement to "
+                      "rel. resid 1e-8",
+          "unknowns": 1769472, "rtol": RTOL, "restart": RESTART, "inner_rtol": INNER_RTOL,
+          "l2": "working set > L2 (GMRES basis 31 x 28 MB), no flush", "parallelism": "replicas"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.proc = None
+        self.uuid = uuid
+
+    def __enter__(self):
+        try:
+            cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd[1:1] = ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_apply(torch, B, mesh, prec, n, iters=40):
+    """Average device time of one operator apply over rotating buffers (> 2x L2)."""
+    dt = torch.complex64 if prec == B.DST_FP32 else torch.complex128
+    esz = 8 if prec == B.DST_FP32 else 16
+    pairs = max(2, int(np.ceil(2 * 135e6 / (2 * n * esz))) + 1)
+    xs = [torch.randn(n, dtype=dt, device="cuda") for _ in range(pairs)]
+    ys = [torch.empty(n, dtype=dt, device="cuda") for _ in range(pairs)]
+    for i in range(pairs):
+        B.dst_apply_operator(mesh, prec, xs[i], ys[i])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(iters):
+        B.dst_apply_operator(mesh, prec, xs[i % pairs], ys[i % pairs])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    return ms, 2.0 * n * esz / (ms * 1e-3) / 1e9
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2103_14588_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = W.zb_2p1(seed=20210326 + rank)
+    mesh_obj = B.Mesh.from_workload(w)
+    mesh = mesh_obj.handle
+    n = mesh_obj.n_unknowns
+    psi = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    opts = {"restart": RESTART, "rtol": RTOL, "max_iters": 200000, "mixed_precision": 1,
+            "inner_rtol": INNER_RTOL, "max_refine": 60}
+
+    for _ in range(args.warmup):
+        B.dst_solve(mesh, opts, psi)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    stats = []
+    prof_opts = dict(opts, profile=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(uuid if rank == 0 else None) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            stats.append(B.dst_solve(mesh, prof_opts, psi))
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+    t_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = tt.item()
+    value = world * args.steps / (t_ms * 1e-3)
+    for s in stats:
+        if s["status"] != 0:
+            raise RuntimeError("timed solve did not converge: %s" % s)
+
+    # per-class kernel accounting over the timed solves
+    tot = {k: [0.0, 0.0, 0.0, 0.0] for k in CLASSES}
+    launches = 0
+    for s in stats:
+        launches += int(s["launches"])
+        for i, k in enumerate(CLASSES):
+            tot[k][0] += s["kernel_ms"][i]
+            tot[k][1] += s["kernel_launches"][i]
+            tot[k][2] += s["kernel_bytes"][i]
+            tot[k][3] += s["kernel_flops"][i]
+    kms = sum(v[0] for v in tot.values())
+
+    if rank != 0:
+        barrier()
+        return
+
+    hbm, hbm_kind = measured_peaks()
+    clocks = clk.summary()
+    mhz = clocks["sm_mhz"] or SM_MAX_MHZ
+    fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s at max clock
+    dom = max(CLASSES, key=lambda k: tot[k][0])
+    d_ms, d_l, d_b, d_f = tot[dom]
+    fp64_classes = ("project", "update", "scale", "misc", "apply64")
+    if dom in fp64_classes and d_f > 0:
+        ach = d_f / (d_ms * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": None,
+                "peak_kind": "FP64 FMA pipe: 152 SMs x 4 FLOP/clk x 2070 MHz (derived; probe measured 1.196)",
+                "achieved_gbs": d_b / (d_ms * 1e-3) / 1e9, "hbm_frac": d_b / (d_ms * 1e-3) / 1e9 / hbm,
+                "avg_launch_us": 1e3 * d_ms / max(d_l, 1)}
+    else:
+        ach = d_b / (d_ms * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_kind": hbm_kind, "avg_launch_us": 1e3 * d_ms / max(d_l, 1)}
+    kernels = {k: {"ms_share": (v[0] / kms if kms else None), "launches": int(v[1]),
+                   "GBps": (v[2] / (v[0] * 1e-3) / 1e9 if v[0] else None),
+                   "TFLOPps": (v[3] / (v[0] * 1e-3) / 1e12 if v[0] else None)} for k, v in tot.items() if v[1]}
+
+    # plain FP64 GMRES(30) on the same system (comparison, outside the timed region)
+    fp64_opts = {"restart": RESTART, "rtol": RTOL, "max_iters": 200000, "mixed_precision": 0}
+    B.dst_solve(mesh, fp64_opts, psi)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    st64 = B.dst_solve(mesh, fp64_opts, psi)
+    f1.record()
+    torch.cuda.synchronize()
+    fp64_s = f0.elapsed_time(f1) * 1e-3
+
+    # standalone operator apply bandwidth (FP32 and FP64)
+    a32_ms, a32_gbs = time_apply(torch, B, mesh, B.DST_FP32, n)
+    a64_ms, a64_gbs = time_apply(torch, B, mesh, B.DST_FP64, n)
+
+    # end to end through the C ABI with host buffers: psi0 from pinned host memory in,
+    # solution to pinned host memory out, every step
+    psi0_host = torch.from_numpy(np.ascontiguousarray(w.psi0).ravel().copy()).pin_memory()
+    out_host = torch.empty(n, dtype=torch.complex128).pin_memory()
+    e2e_steps = min(args.steps, 3)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record()
+    for _ in range(e2e_steps):
+        B.dst_set_initial_data(mesh, psi0_host)
+        B.dst_solve(mesh, opts, psi)
+        out_host.copy_(psi, non_blocking=True)
+    g1.record()
+    torch.cuda.synchronize()
+    e2e_s = g0.elapsed_time(g1) * 1e-3 / e2e_steps
+    e2e = {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(psi0_host.numel() * 16),
+           "d2h_bytes_per_step": int(n * 16)}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        sec_step = oracle_seconds_per_step(w, k=2)
+        n_or = iteration_count("zb_2p1")
+        src = "the oracle's own %s-step solve recorded by oracle/iteration_counts.py" % n_or
+        if n_or is None:
+            n_or = st64["iters"]
+            src = "the %d Arnoldi steps the FP64 GPU GMRES took on this system" % n_or
+        cpu = {"value": 1.0 / (sec_step * n_or), "unit": "solves/s", "cores": host_cores(), "kind": "oracle",
+               "sample": "oracle GMRES(30), FP64 numpy, on the full 96x96x96 system for 1 and 3 Arnoldi steps "
+                         "(difference / 2 = %.3f s per step), times %s" % (sec_step, src)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 apply + f64 orthogonalisation/refinement", "data": "synthetic",
+        "config": CONFIG,
+        "time_to_solution_s": t_ms * 1e-3 / args.steps,
+        "solve": {"iters": stats[-1]["iters"], "restarts": stats[-1]["restarts"],
+                  "refinements": stats[-1]["refinements"], "rel_resid_true": stats[-1]["rel_resid_true"]},
+        "fp64_gmres": {"time_to_solution_s": fp64_s, "iters": st64["iters"], "restarts": st64["restarts"],
+                       "rel_resid_true": st64["rel_resid_true"], "mixed_speedup": fp64_s / (t_ms * 1e-3 / args.steps)},
+        "apply": {"fp32_gbs": a32_gbs, "fp32_us": 1e3 * a32_ms, "fp32_frac_of_hbm": a32_gbs / hbm,
+                  "fp64_gbs": a64_gbs, "fp64_us": 1e3 * a64_ms, "fp64_frac_of_hbm": a64_gbs / hbm,
+                  "hbm_peak": hbm, "peak_kind": hbm_kind, "bytes_per_unknown": {"fp32": 16, "fp64": 32}},
+        "roofline": roof,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    barrier()
+    mesh_obj.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

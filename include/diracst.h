@@ -1,0 +1,218 @@
+/*
+ * diracst.h - C ABI of the GB300 spacetime finite-element Dirac solver.
+ *
+ * The library discretises the Dirac equation (i gamma^mu d_mu - m) Psi = 0
+ * (Sec. 2.1, Eq. 1) on a structured spacetime mesh of Q1 elements
+ * (Sec. 2.2, Eqs. 13-16; 1+1, 2+1 or 3+1), treats the t = 0 layer as known
+ * initial data and solves the remaining square system
+ *     D_w22 Psi_u = -D_w21 Psi_0                         (Sec. 2.1, Eq. 11)
+ * with restarted GMRES (Sec. 2.2; Algorithm 1 steps 5-6).  The operator is
+ * never assembled: it is applied matrix-free by CUDA kernels.
+ *
+ * Conventions shared by every call:
+ *   - Rows of D_w22 are premultiplied by gamma^0 ("Hamiltonian form"):
+ *       A = i D^t (x) I + i sum_k D^k (x) alpha_k - D^0 (x) (m beta + V),
+ *     alpha_k = gamma^0 gamma^k, beta = gamma^0 (Appendix A's element
+ *     matrices D^t, D^k, D^0).  The solution equals that of the printed form;
+ *     GMRES converges only in this one.
+ *   - Gamma matrices: 1+1 gamma^0 = diag(1,-1), gamma^1 = [[0,1],[-1,0]]
+ *     (Appendix A); 2+1 adds gamma^2 = -i sigma_x; 3+1 is the Dirac
+ *     representation.  Spinor components NC = 2 (1+1, 2+1) or 4 (3+1).
+ *   - The potential V is potential energy (i d_t Psi = (H_0 + V) Psi), one
+ *     value per spatial element, constant in time (Sec. 4.3, Eq. 21).
+ *   - Unknown vector layout: index ((((t-1)*nz + z)*ny + y)*nx + x)*NC + c
+ *     for unknown time layers t = 1..N_t, complex interleaved (re, im).
+ *     FP64 vectors are double pairs (16 B per entry), FP32 vectors float
+ *     pairs (8 B).  Axes a mesh does not have count one node.
+ *   - Spatial nodes per axis: PERIODIC n_el (nodes 0..n_el-1), OPEN n_el+1
+ *     (natural boundary), DIRICHLET n_el-1 (homogeneous values at both ends
+ *     are known and removed like the t = 0 layer).
+ *   - Device pointers are CUDA device addresses owned by the caller, on the
+ *     device current when the mesh was created; "stream" is a cudaStream_t
+ *     (NULL = legacy default stream).  Calls enqueue work on that stream and
+ *     return without synchronising unless stated.
+ *   - Every call returns a status code (DST_OK = 0 on success) and never
+ *     aborts the process.  One mesh must not be used by two host threads at
+ *     once.
+ */
+#ifndef DIRACST_H
+#define DIRACST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DST_API __attribute__((visibility("default")))
+#else
+#define DST_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    DST_OK = 0,
+    DST_NOT_CONVERGED = 1,   /* solve hit max_iters; psi holds the best iterate */
+    DST_ERR_ARG = -1,        /* invalid argument (null pointer, bad size, bad enum) */
+    DST_ERR_OOM = -2,        /* device or host allocation failed */
+    DST_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+    DST_ERR_NAN = -5,        /* non-finite value met in the right-hand side or residual */
+    DST_ERR_STATE = -6       /* required input not set yet (e.g. initial data) */
+};
+
+enum { DST_BC_PERIODIC = 0, DST_BC_OPEN = 1, DST_BC_DIRICHLET = 2 };
+enum { DST_FP64 = 0, DST_FP32 = 1 };
+
+typedef struct dst_mesh dst_mesh;   /* opaque, owned by the library */
+
+/*
+ * Create a structured spacetime mesh (Algorithm 1 step 1).
+ *   d       spatial dimension 1, 2 or 3.
+ *   n_el    element counts (x, y, z, t); entries beyond d are ignored except
+ *           n_el[3] = N_t >= 1.  Periodic axes need n_el >= 1, Dirichlet >= 2.
+ *   lo, hi  domain bounds (x, y, z, t), hi > lo on every used axis.
+ *   bc      boundary kind per spatial axis (DST_BC_*), entries beyond d ignored.
+ *   out     receives the mesh.  Mass defaults to 1, potential to zero; the
+ *           initial data must be set before dst_build_rhs / dst_solve.
+ * Errors: DST_ERR_ARG, DST_ERR_CUDA (no device), DST_ERR_OOM.
+ */
+DST_API int dst_create_mesh(int d, const int64_t n_el[4], const double lo[4], const double hi[4],
+                    const int bc[3], dst_mesh **out);
+
+/* Free the mesh and every device buffer it holds.  NULL is accepted. */
+DST_API int dst_destroy_mesh(dst_mesh *mesh);
+
+/*
+ * Sizes: n_spatial_nodes = nodes of one time layer of unknowns,
+ * n_unknowns = N_t * n_spatial_nodes * NC complex entries, ncomp = NC.
+ * Any output pointer may be NULL.
+ */
+DST_API int dst_mesh_sizes(const dst_mesh *mesh, int64_t *n_spatial_nodes, int64_t *n_unknowns,
+                   int *ncomp);
+
+/* Particle mass m in the free Dirac equation (Sec. 2.1, Eq. 1).  Any finite value. */
+DST_API int dst_set_mass(dst_mesh *mesh, double m);
+
+/*
+ * Potential energy per spatial element (Sec. 4.3, Eqs. 21 and 23), copied
+ * from HOST memory: nel_x * nel_y * nel_z doubles, x fastest, each the value
+ * at the element centroid; NULL resets V to zero.  A potential that depends
+ * on x only takes the fast separable path; any other takes a general path.
+ * Errors: DST_ERR_ARG (non-finite value), DST_ERR_OOM, DST_ERR_CUDA.
+ */
+DST_API int dst_set_potential(dst_mesh *mesh, const double *V_elem);
+
+/*
+ * Initial data Psi_0 on the t = 0 layer (the K known spinors of Sec. 2.1,
+ * Eq. 8), copied from HOST memory: n_spatial_nodes * NC complex values
+ * (2 doubles each), same layout as one time layer of the unknown vector.
+ */
+DST_API int dst_set_initial_data(dst_mesh *mesh, const double *psi0);
+
+/*
+ * Right-hand side b = -D_w21 Psi_0 (Sec. 2.1, Eq. 11; Algorithm 1 step 5)
+ * into the caller's DEVICE FP64 vector b (n_unknowns complex).  Only the
+ * first unknown time layer is non-zero; the call writes every entry.
+ * Errors: DST_ERR_STATE (no initial data), DST_ERR_ARG, DST_ERR_CUDA.
+ */
+DST_API int dst_build_rhs(const dst_mesh *mesh, void *b, void *stream);
+
+/*
+ * y = A x with A = D_w22 (Sec. 2.1, Eq. 11; element-by-element sum of
+ * Sec. 2.2 evaluated as a sum-factorised stencil), x and y DEVICE vectors of
+ * n_unknowns complex values in the given precision (DST_FP64: double pairs,
+ * DST_FP32: float pairs, arithmetic in that precision).  x and y must not
+ * overlap.  Errors: DST_ERR_ARG, DST_ERR_CUDA.
+ */
+DST_API int dst_apply_operator(const dst_mesh *mesh, int precision, const void *x, void *y,
+                       void *stream);
+
+/*
+ * Arnoldi projection h = V^H w (the classical Gram-Schmidt inner products of
+ * restarted GMRES, Sec. 2.2): V holds nvec DEVICE FP64 complex vectors of
+ * length n stored one after another (vector j starts at V + j*n), w one more;
+ * h receives nvec complex values (2*nvec doubles) in DEVICE memory.  The sums
+ * are reduced in a fixed order (deterministic).  The call allocates its
+ * reduction scratch from the stream-ordered allocator.  1 <= nvec <= 64.
+ */
+DST_API int dst_arnoldi_project(int64_t n, int nvec, const void *V, const void *w, void *h,
+                        void *stream);
+
+/*
+ * Arnoldi update: w <- w - V h with the same V layout and a DEVICE h of nvec
+ * complex values, and nrm2 (DEVICE, one double) <- ||w||^2 after the update.
+ */
+DST_API int dst_arnoldi_update(int64_t n, int nvec, const void *V, const void *h, void *w,
+                       void *nrm2, void *stream);
+
+typedef struct {
+    int restart;            /* Krylov dimension m of GMRES(m); 1..64, default 30 */
+    int max_iters;          /* total Arnoldi steps across restarts (and refinements) */
+    double rtol;            /* stop when ||b - A x|| <= rtol ||b|| (true residual, FP64) */
+    int mixed_precision;    /* 0: FP64 GMRES; 1: FP64 iterative refinement around an
+                               inner GMRES whose operator apply runs in FP32 */
+    double inner_rtol;      /* inner relative tolerance per refinement step (mixed only) */
+    int max_refine;         /* cap on refinement steps (mixed only) */
+    int use_initial_guess;  /* 1: psi holds x0 on entry; 0: start from zero */
+    int profile;            /* 1: time every kernel class with CUDA events (small overhead) */
+} dst_solve_opts;
+
+/* Kernel classes of dst_solve_stats' per-class arrays. */
+enum {
+    DST_K_APPLY64 = 0,      /* operator apply, FP64 */
+    DST_K_APPLY32 = 1,      /* operator apply, FP32 */
+    DST_K_CAST = 2,         /* FP64 <-> FP32 vector casts around the FP32 apply */
+    DST_K_PROJECT = 3,      /* Arnoldi projection h = V^H w (partials + reduction) */
+    DST_K_UPDATE = 4,       /* Arnoldi update w -= V h (+ norm), x += V y */
+    DST_K_SCALE = 5,        /* basis normalisation */
+    DST_K_MISC = 6,         /* residuals, norms, x += d */
+    DST_K_RHS = 7,          /* right-hand side */
+    DST_NUM_KERNEL_CLASSES = 8
+};
+
+typedef struct {
+    int iters;              /* Arnoldi steps (operator applies inside GMRES cycles) */
+    int restarts;           /* GMRES cycles completed */
+    int refinements;        /* outer refinement steps (mixed only) */
+    int status;             /* same value the call returns */
+    double rel_resid_true;  /* ||b - A x|| / ||b|| in FP64 at exit */
+    double rel_resid_est;   /* last implicit GMRES residual estimate (relative) */
+    double seconds;         /* host wall time of the call (includes synchronisation) */
+    double bytes_moved;     /* algorithmic device bytes of the kernels launched */
+    double launches;        /* kernel launches of the call */
+    double kernel_ms[8];        /* device time per DST_K_* class (opts.profile only, else 0) */
+    double kernel_launches[8];  /* kernel launches per class */
+    double kernel_bytes[8];     /* algorithmic bytes per class (reads + writes) */
+    double kernel_flops[8];     /* algorithmic floating-point operations per class */
+} dst_solve_stats;
+
+/* Fill opts with the defaults (restart 30, max_iters 100000, rtol 1e-8,
+ * FP64, inner_rtol 1e-4, max_refine 50, zero initial guess, no profiling). */
+DST_API int dst_default_solve_opts(dst_solve_opts *opts);
+
+/*
+ * Solve D_w22 psi = -D_w21 Psi_0 (Algorithm 1 step 6) into the caller's
+ * DEVICE FP64 vector psi (n_unknowns complex).  The mesh allocates its GMRES
+ * workspace on first use and keeps it until destroyed.  Synchronises the
+ * stream before returning.  Returns DST_OK, DST_NOT_CONVERGED (psi holds the
+ * last iterate), DST_ERR_NAN, DST_ERR_STATE, DST_ERR_ARG, DST_ERR_OOM or
+ * DST_ERR_CUDA; stats (may be NULL) is filled in every case it can be.
+ */
+DST_API int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, dst_solve_stats *stats,
+              void *stream);
+
+/* Static, human-readable name of a status code. */
+DST_API const char *dst_status_string(int status);
+
+/* Text of the last CUDA failure seen by this host thread (call, file, line,
+ * CUDA message) after a DST_ERR_CUDA return; empty if there was none.  The
+ * pointer stays valid until the next failing call on the same thread. */
+DST_API const char *dst_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIRACST_H */

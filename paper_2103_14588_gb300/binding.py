@@ -1,0 +1,288 @@
+"""ctypes binding of the diracst C ABI (include/diracst.h): argument marshalling only.
+
+Every function here has the name of the C call it wraps and does nothing but
+convert arguments (numpy arrays for host inputs, torch CUDA tensors or raw
+integer addresses for device buffers, the current torch stream by default)
+and turn negative status codes into ``DstError``.  All computation runs in the
+CUDA kernels of ``lib/libdiracst.so``; if that library is missing the import
+fails loudly - there is no CPU fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libdiracst.so")
+
+DST_OK, DST_NOT_CONVERGED = 0, 1
+DST_ERR_ARG, DST_ERR_OOM, DST_ERR_CUDA, DST_ERR_NAN, DST_ERR_STATE = -1, -2, -3, -5, -6
+DST_BC_PERIODIC, DST_BC_OPEN, DST_BC_DIRICHLET = 0, 1, 2
+DST_FP64, DST_FP32 = 0, 1
+
+EXPORTED = (
+    "dst_create_mesh", "dst_destroy_mesh", "dst_mesh_sizes", "dst_set_mass", "dst_set_potential",
+    "dst_set_initial_data", "dst_build_rhs", "dst_apply_operator", "dst_arnoldi_project",
+    "dst_arnoldi_update", "dst_default_solve_opts", "dst_solve", "dst_status_string",
+    "dst_last_error_detail",
+)
+
+
+class DstError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        detail = ""
+        if code == DST_ERR_CUDA and _lib is not None:
+            detail = ": " + _lib.dst_last_error_detail().decode(errors="replace")
+        super().__init__("%s failed with %d (%s)%s" % (where, code, dst_status_string(code), detail))
+
+
+class dst_solve_opts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("mixed_precision", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("max_refine", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+class dst_solve_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("status", ctypes.c_int), ("rel_resid_true", ctypes.c_double),
+                ("rel_resid_est", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("bytes_moved", ctypes.c_double), ("launches", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_double * 8),
+                ("kernel_bytes", ctypes.c_double * 8), ("kernel_flops", ctypes.c_double * 8)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if name.startswith("kernel_") else v
+        return out
+
+
+KERNEL_CLASSES = ("apply64", "apply32", "cast", "project", "update", "scale", "misc", "rhs")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libdiracst.so is not built (%s); run __graft_entry__.build() or "
+                          "python -m paper_2103_14588_gb300.build" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, c_int, c_double = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "dst_create_mesh": (c_int, [c_int, P(i64), P(c_double), P(c_double), P(c_int), P(vp)]),
+        "dst_destroy_mesh": (c_int, [vp]),
+        "dst_mesh_sizes": (c_int, [vp, P(i64), P(i64), P(c_int)]),
+        "dst_set_mass": (c_int, [vp, c_double]),
+        "dst_set_potential": (c_int, [vp, vp]),
+        "dst_set_initial_data": (c_int, [vp, vp]),
+        "dst_build_rhs": (c_int, [vp, vp, vp]),
+        "dst_apply_operator": (c_int, [vp, c_int, vp, vp, vp]),
+        "dst_arnoldi_project": (c_int, [i64, c_int, vp, vp, vp, vp]),
+        "dst_arnoldi_update": (c_int, [i64, c_int, vp, vp, vp, vp, vp]),
+        "dst_default_solve_opts": (c_int, [P(dst_solve_opts)]),
+        "dst_solve": (c_int, [vp, P(dst_solve_opts), vp, P(dst_solve_stats), vp]),
+        "dst_status_string": (ctypes.c_char_p, [c_int]),
+        "dst_last_error_detail": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+_lib = _load()
+
+
+def library():
+    return _lib
+
+
+# ---- marshalling helpers -------------------------------------------------
+
+def _dev_ptr(t, dtype=None, numel=None, what="buffer"):
+    """Device address of a torch CUDA tensor (checked) or a raw integer address."""
+    if isinstance(t, int):
+        return t
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor or an integer device address" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must have dtype %s, got %s" % (what, dtype, t.dtype))
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s holds %d elements, needs %d" % (what, t.numel(), numel))
+    return t.data_ptr()
+
+
+def _stream(stream, *tensors):
+    if stream is None:
+        for t in tensors:
+            if not isinstance(t, int):
+                import torch
+                return torch.cuda.current_stream(t.device).cuda_stream
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc, where):
+    if rc < 0:
+        raise DstError(rc, where)
+    return rc
+
+
+# ---- the C ABI, one wrapper per call --------------------------------------
+
+def dst_status_string(code):
+    return _lib.dst_status_string(int(code)).decode()
+
+
+def dst_create_mesh(d, n_el, lo, hi, bc):
+    """Returns an opaque mesh handle (int).  n_el, lo, hi: 4 entries (x, y, z, t); bc: 3."""
+    n = (ctypes.c_int64 * 4)(*[int(v) for v in n_el])
+    a = (ctypes.c_double * 4)(*[float(v) for v in lo])
+    b = (ctypes.c_double * 4)(*[float(v) for v in hi])
+    c = (ctypes.c_int * 3)(*[int(v) for v in (list(bc) + [0, 0, 0])[:3]])
+    out = ctypes.c_void_p()
+    _check(_lib.dst_create_mesh(int(d), n, a, b, c, ctypes.byref(out)), "dst_create_mesh")
+    return out.value
+
+
+def dst_destroy_mesh(mesh):
+    return _check(_lib.dst_destroy_mesh(mesh), "dst_destroy_mesh")
+
+
+def dst_mesh_sizes(mesh):
+    ns, nu, nc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    _check(_lib.dst_mesh_sizes(mesh, ctypes.byref(ns), ctypes.byref(nu), ctypes.byref(nc)), "dst_mesh_sizes")
+    return ns.value, nu.value, nc.value
+
+
+def dst_set_mass(mesh, m):
+    return _check(_lib.dst_set_mass(mesh, float(m)), "dst_set_mass")
+
+
+def dst_set_potential(mesh, V):
+    if V is None:
+        return _check(_lib.dst_set_potential(mesh, None), "dst_set_potential")
+    arr = np.ascontiguousarray(V, dtype=np.float64)
+    return _check(_lib.dst_set_potential(mesh, arr.ctypes.data), "dst_set_potential")
+
+
+def dst_set_initial_data(mesh, psi0):
+    """psi0: host data - a numpy array or a CPU torch tensor (e.g. pinned), complex128."""
+    ns, _, nc = dst_mesh_sizes(mesh)
+    if type(psi0).__module__.startswith("torch"):
+        import torch
+        if psi0.is_cuda or psi0.dtype != torch.complex128 or not psi0.is_contiguous():
+            raise TypeError("psi0 must be a contiguous complex128 host tensor")
+        if psi0.numel() != ns * nc:
+            raise ValueError("psi0 needs %d complex values, got %d" % (ns * nc, psi0.numel()))
+        return _check(_lib.dst_set_initial_data(mesh, psi0.data_ptr()), "dst_set_initial_data")
+    arr = np.ascontiguousarray(psi0, dtype=np.complex128).ravel()
+    if arr.size != ns * nc:
+        raise ValueError("psi0 needs %d complex values, got %d" % (ns * nc, arr.size))
+    return _check(_lib.dst_set_initial_data(mesh, arr.ctypes.data), "dst_set_initial_data")
+
+
+def dst_build_rhs(mesh, b, stream=None):
+    import torch
+    _, nu, _ = dst_mesh_sizes(mesh)
+    p = _dev_ptr(b, torch.complex128, nu, "b")
+    return _check(_lib.dst_build_rhs(mesh, p, _stream(stream, b)), "dst_build_rhs")
+
+
+def dst_apply_operator(mesh, precision, x, y, stream=None):
+    import torch
+    _, nu, _ = dst_mesh_sizes(mesh)
+    dt = torch.complex128 if precision == DST_FP64 else torch.complex64
+    px = _dev_ptr(x, dt, nu, "x")
+    py = _dev_ptr(y, dt, nu, "y")
+    return _check(_lib.dst_apply_operator(mesh, int(precision), px, py, _stream(stream, x, y)),
+                  "dst_apply_operator")
+
+
+def dst_arnoldi_project(n, nvec, V, w, h, stream=None):
+    import torch
+    pV = _dev_ptr(V, torch.complex128, n * nvec, "V")
+    pw = _dev_ptr(w, torch.complex128, n, "w")
+    ph = _dev_ptr(h, torch.complex128, nvec, "h")
+    return _check(_lib.dst_arnoldi_project(int(n), int(nvec), pV, pw, ph, _stream(stream, V, w, h)),
+                  "dst_arnoldi_project")
+
+
+def dst_arnoldi_update(n, nvec, V, h, w, nrm2, stream=None):
+    import torch
+    pV = _dev_ptr(V, torch.complex128, n * nvec, "V")
+    ph = _dev_ptr(h, torch.complex128, nvec, "h")
+    pw = _dev_ptr(w, torch.complex128, n, "w")
+    pn = _dev_ptr(nrm2, torch.float64, 1, "nrm2")
+    return _check(_lib.dst_arnoldi_update(int(n), int(nvec), pV, ph, pw, pn, _stream(stream, V, w)),
+                  "dst_arnoldi_update")
+
+
+def dst_default_solve_opts():
+    o = dst_solve_opts()
+    _check(_lib.dst_default_solve_opts(ctypes.byref(o)), "dst_default_solve_opts")
+    return o
+
+
+def dst_solve(mesh, opts, psi, stream=None):
+    """Solve into psi (complex128 CUDA tensor).  opts: dst_solve_opts or dict of overrides.
+
+    Returns the stats as a dict; raises DstError on an error status (not on
+    DST_NOT_CONVERGED, which is reported in stats["status"]).
+    """
+    import torch
+    o = opts if isinstance(opts, dst_solve_opts) else dst_default_solve_opts()
+    if isinstance(opts, dict):
+        for k, v in opts.items():
+            setattr(o, k, v)
+    _, nu, _ = dst_mesh_sizes(mesh)
+    p = _dev_ptr(psi, torch.complex128, nu, "psi")
+    st = dst_solve_stats()
+    rc = _lib.dst_solve(mesh, ctypes.byref(o), p, ctypes.byref(st), _stream(stream, psi))
+    _check(rc, "dst_solve")
+    return st.as_dict()
+
+
+class Mesh:
+    """Owning wrapper of a mesh handle built from a workload-like description."""
+
+    def __init__(self, d, n_el, lo, hi, bc, m=None, V=None, psi0=None):
+        self.handle = dst_create_mesh(d, n_el, lo, hi, bc)
+        self.n_spatial, self.n_unknowns, self.ncomp = dst_mesh_sizes(self.handle)
+        if m is not None:
+            dst_set_mass(self.handle, m)
+        if V is not None:
+            dst_set_potential(self.handle, V)
+        if psi0 is not None:
+            dst_set_initial_data(self.handle, psi0)
+
+    @classmethod
+    def from_workload(cls, w):
+        return cls(w.d, w.n_el, w.lo, w.hi, w.bc, m=w.m, V=w.V, psi0=w.psi0)
+
+    def close(self):
+        if self.handle:
+            dst_destroy_mesh(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,12 @@
+// Operator apply and right-hand side instantiated for 1+1 dimensions (NC = 2).
+#include "apply_impl.cuh"
+
+int dst_launch_apply_d1(const OpParams &p, int precision, const void *x, void *y, cudaStream_t s) {
+    if (precision == DST_FP64)
+        return dst::launch_apply<1, 2, double>(p, (const double2 *)x, (double2 *)y, s);
+    return dst::launch_apply<1, 2, float>(p, (const float2 *)x, (float2 *)y, s);
+}
+
+int dst_launch_rhs_d1(const OpParams &p, const double2 *psi0, double2 *b, cudaStream_t s) {
+    return dst::launch_rhs<1, 2>(p, psi0, b, s);
+}

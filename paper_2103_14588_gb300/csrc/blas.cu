@@ -1,0 +1,290 @@
+// Vector kernels of restarted GMRES (Saad & Schultz 1986, the Krylov solver
+// of Sec. 2.2): the classical Gram-Schmidt projection h = V^H w, the update
+// w <- w - V h fused with ||w||^2, scaling, residuals and precision casts.
+//
+// Reductions are deterministic: each CTA owns a fixed contiguous slice of the
+// vector, threads accumulate their elements in a fixed order, warps reduce by
+// a fixed shuffle tree, CTAs write partials that a second kernel sums in CTA
+// order.  All arithmetic of these kernels is FP64.
+#include "blas.h"
+
+namespace dst {
+
+static constexpr int RED_THREADS = 256;
+static constexpr int PROJ_GROUP = 8;     // basis vectors per register group
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum of one double (result valid in thread 0); fixed order.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
+    return r;
+}
+
+__device__ __forceinline__ void slice(int64_t n, int64_t &b, int64_t &e) {
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    b = (int64_t)blockIdx.x * per;
+    e = b + per < n ? b + per : n;
+}
+
+// partials[blk * nvec + j] = sum over the CTA's slice of conj(V_j) w.
+__global__ void __launch_bounds__(RED_THREADS)
+project_partial_kernel(int64_t n, int nvec, const double2 *__restrict__ V, const double2 *__restrict__ w,
+                       double2 *__restrict__ partials) {
+    __shared__ double sh[RED_THREADS / 32];
+    int64_t b, e;
+    slice(n, b, e);
+    for (int j0 = 0; j0 < nvec; j0 += PROJ_GROUP) {
+        const int gv = nvec - j0 < PROJ_GROUP ? nvec - j0 : PROJ_GROUP;
+        double ar[PROJ_GROUP], ai[PROJ_GROUP];
+#pragma unroll
+        for (int g = 0; g < PROJ_GROUP; ++g) { ar[g] = 0.0; ai[g] = 0.0; }
+        for (int64_t i = b + threadIdx.x; i < e; i += RED_THREADS) {
+            const double2 wi = w[i];
+#pragma unroll
+            for (int g = 0; g < PROJ_GROUP; ++g) {
+                if (g < gv) {
+                    const double2 v = V[(int64_t)(j0 + g) * n + i];
+                    ar[g] = fma(v.x, wi.x, fma(v.y, wi.y, ar[g]));
+                    ai[g] = fma(v.x, wi.y, fma(-v.y, wi.x, ai[g]));
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < PROJ_GROUP; ++g) {
+            if (g < gv) {
+                double sr = block_sum(ar[g], sh);
+                double si = block_sum(ai[g], sh);
+                if (threadIdx.x == 0) partials[(int64_t)blockIdx.x * nvec + j0 + g] = make_double2(sr, si);
+            }
+        }
+    }
+}
+
+// out[j] = sum_blk partials[blk * nvec + j]   (one CTA per j)
+__global__ void __launch_bounds__(RED_THREADS)
+reduce_partials_kernel(int nblk, int nvec, const double2 *__restrict__ partials, double2 *__restrict__ out) {
+    __shared__ double sh[RED_THREADS / 32];
+    const int j = blockIdx.x;
+    double sr = 0.0, si = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += RED_THREADS) {
+        const double2 v = partials[(int64_t)k * nvec + j];
+        sr += v.x;
+        si += v.y;
+    }
+    sr = block_sum(sr, sh);
+    si = block_sum(si, sh);
+    if (threadIdx.x == 0) out[j] = make_double2(sr, si);
+}
+
+// w <- w - sum_j V_j h_j ; partial ||w||^2 per CTA.
+__global__ void __launch_bounds__(RED_THREADS)
+update_kernel(int64_t n, int nvec, const double2 *__restrict__ V, const double2 *__restrict__ h,
+              double2 *__restrict__ w, double *__restrict__ nrm_partials) {
+    __shared__ double2 hs[DST_MAX_VEC];
+    __shared__ double sh[RED_THREADS / 32];
+    for (int j = threadIdx.x; j < nvec; j += RED_THREADS) hs[j] = h[j];
+    __syncthreads();
+    int64_t b, e;
+    slice(n, b, e);
+    double nr = 0.0;
+    for (int64_t i = b + threadIdx.x; i < e; i += RED_THREADS) {
+        double2 acc = w[i];
+        for (int j = 0; j < nvec; ++j) {
+            const double2 v = V[(int64_t)j * n + i];
+            const double2 c = hs[j];
+            acc.x = fma(-v.x, c.x, fma(v.y, c.y, acc.x));
+            acc.y = fma(-v.x, c.y, fma(-v.y, c.x, acc.y));
+        }
+        w[i] = acc;
+        nr = fma(acc.x, acc.x, fma(acc.y, acc.y, nr));
+    }
+    nr = block_sum(nr, sh);
+    if (threadIdx.x == 0 && nrm_partials) nrm_partials[blockIdx.x] = nr;
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+reduce_real_kernel(int nblk, const double *__restrict__ partials, double *__restrict__ out) {
+    __shared__ double sh[RED_THREADS / 32];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += RED_THREADS) s += partials[k];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// ||x||^2 partials
+__global__ void __launch_bounds__(RED_THREADS)
+nrm2_partial_kernel(int64_t n, const double2 *__restrict__ x, double *__restrict__ partials) {
+    __shared__ double sh[RED_THREADS / 32];
+    int64_t b, e;
+    slice(n, b, e);
+    double s = 0.0;
+    for (int64_t i = b + threadIdx.x; i < e; i += RED_THREADS) {
+        const double2 v = x[i];
+        s = fma(v.x, v.x, fma(v.y, v.y, s));
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// r = b - y ; ||r||^2 partials
+__global__ void __launch_bounds__(RED_THREADS)
+residual_kernel(int64_t n, const double2 *__restrict__ b_, const double2 *__restrict__ y, double2 *__restrict__ r,
+                double *__restrict__ partials) {
+    __shared__ double sh[RED_THREADS / 32];
+    int64_t b, e;
+    slice(n, b, e);
+    double s = 0.0;
+    for (int64_t i = b + threadIdx.x; i < e; i += RED_THREADS) {
+        const double2 u = b_[i], v = y[i];
+        const double2 d = make_double2(u.x - v.x, u.y - v.y);
+        r[i] = d;
+        s = fma(d.x, d.x, fma(d.y, d.y, s));
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// dst = src * (1/sqrt(*nrm2)) (or * scale when nrm2 is null)
+__global__ void scale_kernel(int64_t n, const double2 *__restrict__ src, double2 *__restrict__ dst,
+                             const double *__restrict__ nrm2, double scale) {
+    const double s = nrm2 ? 1.0 / sqrt(*nrm2) : scale;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = src[i];
+        dst[i] = make_double2(v.x * s, v.y * s);
+    }
+}
+
+__global__ void cast_64_32_kernel(int64_t n, const double2 *__restrict__ src, float2 *__restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = src[i];
+        dst[i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+__global__ void cast_32_64_kernel(int64_t n, const float2 *__restrict__ src, double2 *__restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = src[i];
+        dst[i] = make_double2((double)v.x, (double)v.y);
+    }
+}
+
+// x += d
+__global__ void axpy1_kernel(int64_t n, const double2 *__restrict__ d, double2 *__restrict__ x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 a = x[i], b = d[i];
+        x[i] = make_double2(a.x + b.x, a.y + b.y);
+    }
+}
+
+}  // namespace dst
+
+using namespace dst;
+
+static unsigned stream_blocks(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+int dst_k_project(int64_t n, int nvec, const double2 *V, const double2 *w, double2 *h, double2 *partials,
+                  int nblk, cudaStream_t s) {
+    project_partial_kernel<<<nblk, RED_THREADS, 0, s>>>(n, nvec, V, w, partials);
+    reduce_partials_kernel<<<nvec, RED_THREADS, 0, s>>>(nblk, nvec, partials, h);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_update(int64_t n, int nvec, const double2 *V, const double2 *h, double2 *w, double *nrm2,
+                 double *partials, int nblk, cudaStream_t s) {
+    update_kernel<<<nblk, RED_THREADS, 0, s>>>(n, nvec, V, h, w, nrm2 ? partials : nullptr);
+    if (nrm2) reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, nrm2);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_nrm2(int64_t n, const double2 *x, double *nrm2, double *partials, int nblk, cudaStream_t s) {
+    nrm2_partial_kernel<<<nblk, RED_THREADS, 0, s>>>(n, x, partials);
+    reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, nrm2);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_residual(int64_t n, const double2 *b, const double2 *y, double2 *r, double *nrm2, double *partials,
+                   int nblk, cudaStream_t s) {
+    residual_kernel<<<nblk, RED_THREADS, 0, s>>>(n, b, y, r, partials);
+    reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, nrm2);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_scale(int64_t n, const double2 *src, double2 *dst, const double *nrm2, double scale, cudaStream_t s) {
+    scale_kernel<<<stream_blocks(n), 256, 0, s>>>(n, src, dst, nrm2, scale);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_cast_64_32(int64_t n, const double2 *src, float2 *dst, cudaStream_t s) {
+    cast_64_32_kernel<<<stream_blocks(n), 256, 0, s>>>(n, src, dst);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_cast_32_64(int64_t n, const float2 *src, double2 *dst, cudaStream_t s) {
+    cast_32_64_kernel<<<stream_blocks(n), 256, 0, s>>>(n, src, dst);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_axpy1(int64_t n, const double2 *d, double2 *x, cudaStream_t s) {
+    axpy1_kernel<<<stream_blocks(n), 256, 0, s>>>(n, d, x);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_reduction_blocks(int64_t n) {
+    int64_t b = (n + 1023) / 1024;
+    if (b > DST_MAX_RED_BLOCKS) b = DST_MAX_RED_BLOCKS;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// ---- C ABI wrappers -------------------------------------------------------
+
+extern "C" int dst_arnoldi_project(int64_t n, int nvec, const void *V, const void *w, void *h, void *stream) {
+    if (n < 1 || nvec < 1 || nvec > DST_MAX_VEC || !V || !w || !h) return DST_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nblk = dst_reduction_blocks(n);
+    void *partials = nullptr;
+    if (cudaMallocAsync(&partials, sizeof(double2) * (size_t)nblk * nvec, s) != cudaSuccess) return DST_ERR_OOM;
+    int rc = dst_k_project(n, nvec, (const double2 *)V, (const double2 *)w, (double2 *)h, (double2 *)partials, nblk, s);
+    cudaError_t e = cudaFreeAsync(partials, s);
+    if (rc != DST_OK) return rc;
+    DST_CUDA_TRY(e);
+    return DST_OK;
+}
+
+extern "C" int dst_arnoldi_update(int64_t n, int nvec, const void *V, const void *h, void *w, void *nrm2,
+                                  void *stream) {
+    if (n < 1 || nvec < 1 || nvec > DST_MAX_VEC || !V || !w || !h || !nrm2) return DST_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nblk = dst_reduction_blocks(n);
+    void *partials = nullptr;
+    if (cudaMallocAsync(&partials, sizeof(double) * (size_t)nblk, s) != cudaSuccess) return DST_ERR_OOM;
+    int rc = dst_k_update(n, nvec, (const double2 *)V, (const double2 *)h, (double2 *)w, (double *)nrm2,
+                          (double *)partials, nblk, s);
+    cudaError_t e = cudaFreeAsync(partials, s);
+    if (rc != DST_OK) return rc;
+    DST_CUDA_TRY(e);
+    return DST_OK;
+}

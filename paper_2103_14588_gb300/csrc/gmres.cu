@@ -1,0 +1,435 @@
+// Restarted GMRES(m) and FP32-apply iterative refinement around it
+// (Algorithm 1 step 6: "solve the linear system by utilizing KSP"; the
+// Krylov method is GMRES, Saad & Schultz 1986, named in Sec. 2.2).
+//
+// Arnoldi uses classical Gram-Schmidt applied twice (CGS2): each pass is one
+// projection h = V^H w and one update w <- w - V h over the whole basis, so a
+// step reads the basis twice per pass instead of once per vector (MGS).  The
+// Hessenberg column goes to the host, which applies the Givens rotations and
+// tracks the least-squares residual |g_{j+1}|.  Every restart recomputes the
+// true residual b - A x in FP64.
+//
+// Mixed precision (iterative refinement): the outer loop keeps x, the
+// residual r = b - A x and the convergence test in FP64; each correction d
+// solves A d = r approximately with the same GMRES, whose operator apply
+// runs in FP32 (inputs rounded to FP32, output widened back to FP64), while
+// orthogonalisation, Givens rotations and the least-squares update stay FP64.
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "blas.h"
+#include "internal.h"
+
+namespace {
+
+using cplx = std::complex<double>;
+
+struct Workspace {
+    int64_t n;
+    int m;
+    bool mixed;
+    double2 *V, *b, *tmp, *d, *r64, *h1, *h2;
+    float2 *x32, *y32;
+    double *nrm;
+    double2 *partials_c;
+    double *partials_r;
+    double *host;      // pinned, 2 * 2 * (m + 1) + 8 doubles
+    void *dev_base;
+};
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w) {
+    const int64_t n = mesh->n_unknowns;
+    const int nblk = DST_MAX_RED_BLOCKS;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
+    const size_t oV = take(sizeof(double2) * (size_t)n * (m + 1));
+    const size_t ob = take(sizeof(double2) * n);
+    const size_t ot = take(sizeof(double2) * n);
+    const size_t od = mixed ? take(sizeof(double2) * n) : 0;
+    const size_t or64 = mixed ? take(sizeof(double2) * n) : 0;
+    const size_t ox32 = mixed ? take(sizeof(float2) * n) : 0;
+    const size_t oy32 = mixed ? take(sizeof(float2) * n) : 0;
+    const size_t oh1 = take(sizeof(double2) * DST_MAX_VEC);
+    const size_t oh2 = take(sizeof(double2) * DST_MAX_VEC);
+    const size_t onrm = take(sizeof(double) * 8);
+    const size_t opc = take(sizeof(double2) * (size_t)nblk * DST_MAX_VEC);
+    const size_t opr = take(sizeof(double) * (size_t)nblk);
+    const size_t total = off;
+    if (mesh->ws_bytes < total) {
+        cudaFree(mesh->ws);
+        mesh->ws = nullptr;
+        mesh->ws_bytes = 0;
+        if (cudaMalloc(&mesh->ws, total) != cudaSuccess) {
+            mesh->ws = nullptr;
+            cudaGetLastError();
+            return DST_ERR_OOM;
+        }
+        mesh->ws_bytes = total;
+    }
+    char *base = (char *)mesh->ws;
+    w.n = n;
+    w.m = m;
+    w.mixed = mixed;
+    w.dev_base = base;
+    w.V = (double2 *)(base + oV);
+    w.b = (double2 *)(base + ob);
+    w.tmp = (double2 *)(base + ot);
+    w.d = mixed ? (double2 *)(base + od) : nullptr;
+    w.r64 = mixed ? (double2 *)(base + or64) : nullptr;
+    w.x32 = mixed ? (float2 *)(base + ox32) : nullptr;
+    w.y32 = mixed ? (float2 *)(base + oy32) : nullptr;
+    w.h1 = (double2 *)(base + oh1);
+    w.h2 = (double2 *)(base + oh2);
+    w.nrm = (double *)(base + onrm);
+    w.partials_c = (double2 *)(base + opc);
+    w.partials_r = (double *)(base + opr);
+    return DST_OK;
+}
+
+// Kernel classes reported in dst_solve_stats (index = DST_K_* in diracst.h).
+enum { K_APPLY64 = 0, K_APPLY32, K_CAST, K_PROJECT, K_UPDATE, K_SCALE, K_MISC, K_RHS, K_NCLASS };
+
+// Per-class accounting of launches, algorithmic bytes / flops and, when
+// profiling, device time from CUDA events recorded around each launch on the
+// solver's stream (harvested at the solver's host synchronisation points).
+struct Prof {
+    bool on = false;
+    double ms[K_NCLASS] = {}, launches[K_NCLASS] = {}, bytes[K_NCLASS] = {}, flops[K_NCLASS] = {};
+    struct Pending { int cls; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void harvest() {
+        for (auto &p : pending) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.cls] += t;
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+    ~Prof() {
+        for (auto &p : pending) { pool.push_back(p.a); pool.push_back(p.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+struct Solver {
+    dst_mesh *mesh;
+    cudaStream_t s;
+    Workspace w;
+    int nblk;
+    double bytes = 0.0;
+    int iters = 0;
+    int restarts = 0;
+    double resid_est = 0.0;
+    Prof prof;
+
+    // Run one launcher (nk kernels) of class cls with its algorithmic bytes / flops.
+    template <typename F>
+    int run(int cls, int nk, double nbytes, double nflops, F &&launch) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (prof.on) { a = prof.get(); cudaEventRecord(a, s); }
+        int rc = launch();
+        if (prof.on) {
+            b = prof.get();
+            cudaEventRecord(b, s);
+            prof.pending.push_back({cls, a, b});
+        }
+        prof.launches[cls] += nk;
+        prof.bytes[cls] += nbytes;
+        prof.flops[cls] += nflops;
+        bytes += nbytes;
+        return rc;
+    }
+
+    // out = A in, FP64 or FP32 arithmetic
+    int apply(int prec, const double2 *in, double2 *out) {
+        const double n = (double)w.n;
+        if (prec == DST_FP64)
+            return run(K_APPLY64, 1, 32.0 * n, 0.0, [&] { return dst_internal_apply(mesh, DST_FP64, in, out, s); });
+        int rc = run(K_CAST, 1, 24.0 * n, 0.0, [&] { return dst_k_cast_64_32(w.n, in, w.x32, s); });
+        if (rc) return rc;
+        rc = run(K_APPLY32, 1, 16.0 * n, 0.0, [&] { return dst_internal_apply(mesh, DST_FP32, w.x32, w.y32, s); });
+        if (rc) return rc;
+        return run(K_CAST, 1, 24.0 * n, 0.0, [&] { return dst_k_cast_32_64(w.n, w.y32, out, s); });
+    }
+    int project(int nv, const double2 *wv, double2 *h) {
+        const double n = (double)w.n;
+        return run(K_PROJECT, 2, 16.0 * n * (nv + 1), 8.0 * n * nv,
+                   [&] { return dst_k_project(w.n, nv, w.V, wv, h, w.partials_c, nblk, s); });
+    }
+    int update(int nv, const double2 *h, double2 *x, double *nrm2) {
+        const double n = (double)w.n;
+        return run(K_UPDATE, nrm2 ? 2 : 1, 16.0 * n * (nv + 2), 8.0 * n * nv + (nrm2 ? 4.0 * n : 0.0),
+                   [&] { return dst_k_update(w.n, nv, w.V, h, x, nrm2, w.partials_r, nblk, s); });
+    }
+    int scale(double2 *v) {
+        return run(K_SCALE, 1, 32.0 * w.n, 2.0 * w.n, [&] { return dst_k_scale(w.n, v, v, w.nrm, 0.0, s); });
+    }
+    int residual(const double2 *rhs, const double2 *y, double2 *r, double *nrm2) {
+        return run(K_MISC, 2, 48.0 * w.n, 6.0 * w.n,
+                   [&] { return dst_k_residual(w.n, rhs, y, r, nrm2, w.partials_r, nblk, s); });
+    }
+
+    int read_host(const void *src, size_t bytes_, double *dst) {
+        DST_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes_, cudaMemcpyDeviceToHost, s));
+        return DST_OK;
+    }
+
+    int sync() {
+        DST_CUDA_TRY(cudaStreamSynchronize(s));
+        if (prof.on) prof.harvest();
+        return DST_OK;
+    }
+
+    // ||v||^2 into w.nrm[slot] (device), then the value on the host.
+    int norm(const double2 *v, int slot, double &out) {
+        int rc = run(K_MISC, 2, 16.0 * w.n, 4.0 * w.n,
+                     [&] { return dst_k_nrm2(w.n, v, w.nrm + slot, w.partials_r, nblk, s); });
+        if (rc) return rc;
+        if ((rc = read_host(w.nrm + slot, sizeof(double), w.host)) || (rc = sync())) return rc;
+        out = std::sqrt(w.host[0]);
+        return DST_OK;
+    }
+
+    // V[0] = rhs - A x and beta = ||V[0]|| (x_zero: V[0] = rhs).
+    int initial_residual(int prec, const double2 *x, const double2 *rhs, bool x_zero, double &beta) {
+        int rc;
+        if (x_zero) {
+            DST_CUDA_TRY(cudaMemcpyAsync(w.V, rhs, sizeof(double2) * w.n, cudaMemcpyDeviceToDevice, s));
+            bytes += 32.0 * w.n;
+            return norm(w.V, 0, beta);
+        }
+        if ((rc = apply(prec, x, w.tmp))) return rc;
+        if ((rc = residual(rhs, w.tmp, w.V, w.nrm))) return rc;
+        if ((rc = read_host(w.nrm, sizeof(double), w.host)) || (rc = sync())) return rc;
+        beta = std::sqrt(w.host[0]);
+        return DST_OK;
+    }
+
+    // Restarted GMRES(m) on A_prec x = rhs until ||rhs - A x|| <= tol_abs or
+    // max_iters Arnoldi steps in total (counted in this->iters).
+    int gmres(int prec, double2 *x, const double2 *rhs, bool x_zero, double tol_abs, int max_iters,
+              double &beta_out) {
+        const int m = w.m;
+        const int64_t n = w.n;
+        double beta;
+        int rc = initial_residual(prec, x, rhs, x_zero, beta);
+        if (rc) return rc;
+        if (!std::isfinite(beta)) return DST_ERR_NAN;
+        std::vector<cplx> H((size_t)(m + 1) * m), g(m + 1), sn(m), y(m);
+        std::vector<double> cs(m);
+        auto Hat = [&](int i, int j) -> cplx & { return H[(size_t)i * m + j]; };
+        bool breakdown = false;
+        while (beta > tol_abs && iters < max_iters && !breakdown) {
+            if ((rc = scale(w.V))) return rc;   // V0 = r / beta
+            std::fill(g.begin(), g.end(), cplx(0.0));
+            std::fill(H.begin(), H.end(), cplx(0.0));
+            g[0] = beta;
+            int k = 0;
+            for (int j = 0; j < m; ++j) {
+                double2 *vj = w.V + (size_t)j * n;
+                double2 *wv = w.V + (size_t)(j + 1) * n;
+                if ((rc = apply(prec, vj, wv))) return rc;
+                const int nv = j + 1;
+                // CGS2: two projection + update passes
+                if ((rc = project(nv, wv, w.h1))) return rc;
+                if ((rc = update(nv, w.h1, wv, nullptr))) return rc;
+                if ((rc = project(nv, wv, w.h2))) return rc;
+                if ((rc = update(nv, w.h2, wv, w.nrm))) return rc;
+                // normalise on the device straight away (1/sqrt(nrm)), then read the column
+                if ((rc = scale(wv))) return rc;
+                DST_CUDA_TRY(cudaMemcpyAsync(w.host, w.h1, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
+                DST_CUDA_TRY(cudaMemcpyAsync(w.host + 2 * DST_MAX_VEC, w.h2, sizeof(double2) * nv,
+                                             cudaMemcpyDeviceToHost, s));
+                DST_CUDA_TRY(cudaMemcpyAsync(w.host + 4 * DST_MAX_VEC, w.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+                if ((rc = sync())) return rc;
+                ++iters;
+                double colsq = 0.0;
+                for (int i = 0; i < nv; ++i) {
+                    cplx hv(w.host[2 * i] + w.host[2 * DST_MAX_VEC + 2 * i],
+                            w.host[2 * i + 1] + w.host[2 * DST_MAX_VEC + 2 * i + 1]);
+                    Hat(i, j) = hv;
+                    colsq += std::norm(hv);
+                }
+                const double hn2 = w.host[4 * DST_MAX_VEC];
+                if (!std::isfinite(hn2) || !std::isfinite(colsq)) return DST_ERR_NAN;
+                const double hn = std::sqrt(hn2);
+                Hat(j + 1, j) = hn;
+                for (int i = 0; i < j; ++i) {           // previous rotations
+                    cplx t = cs[i] * Hat(i, j) + sn[i] * Hat(i + 1, j);
+                    Hat(i + 1, j) = -std::conj(sn[i]) * Hat(i, j) + cs[i] * Hat(i + 1, j);
+                    Hat(i, j) = t;
+                }
+                // new rotation zeroing H(j+1, j)
+                const cplx a = Hat(j, j), bb = Hat(j + 1, j);
+                if (std::abs(bb) == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+                else if (std::abs(a) == 0.0) { cs[j] = 0.0; sn[j] = 1.0; }
+                else {
+                    const double rho = std::sqrt(std::norm(a) + std::norm(bb));
+                    cs[j] = std::abs(a) / rho;
+                    sn[j] = (a / std::abs(a)) * std::conj(bb) / rho;
+                }
+                Hat(j, j) = cs[j] * a + sn[j] * bb;
+                Hat(j + 1, j) = 0.0;
+                g[j + 1] = -std::conj(sn[j]) * g[j];
+                g[j] = cs[j] * g[j];
+                k = j + 1;
+                resid_est = std::abs(g[j + 1]);
+                if (hn <= 1e-14 * std::sqrt(colsq + hn2)) { breakdown = true; break; }
+                if (resid_est <= tol_abs || iters >= max_iters) break;
+            }
+            // y = H(0:k,0:k)^{-1} g(0:k), back substitution; x += V y (update with h = -y)
+            for (int i = k - 1; i >= 0; --i) {
+                cplx acc = g[i];
+                for (int l = i + 1; l < k; ++l) acc -= Hat(i, l) * y[l];
+                y[i] = acc / Hat(i, i);
+            }
+            for (int i = 0; i < k; ++i) {
+                w.host[2 * i] = -y[i].real();
+                w.host[2 * i + 1] = -y[i].imag();
+            }
+            DST_CUDA_TRY(cudaMemcpyAsync(w.h1, w.host, sizeof(double2) * k, cudaMemcpyHostToDevice, s));
+            if ((rc = update(k, w.h1, x, nullptr))) return rc;
+            ++restarts;
+            if ((rc = initial_residual(prec, x, rhs, false, beta))) return rc;
+            if (!std::isfinite(beta)) return DST_ERR_NAN;
+        }
+        beta_out = beta;
+        return DST_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" int dst_default_solve_opts(dst_solve_opts *o) {
+    if (!o) return DST_ERR_ARG;
+    o->restart = 30;
+    o->max_iters = 100000;
+    o->rtol = 1e-8;
+    o->mixed_precision = 0;
+    o->inner_rtol = 1e-4;
+    o->max_refine = 50;
+    o->use_initial_guess = 0;
+    o->profile = 0;
+    return DST_OK;
+}
+
+static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst_solve_stats &st,
+                      cudaStream_t s) {
+    const bool mixed = o.mixed_precision != 0;
+    Solver sv;
+    sv.mesh = mesh;
+    sv.s = s;
+    sv.nblk = dst_reduction_blocks(mesh->n_unknowns);
+    int rc = setup_workspace(mesh, o.restart, mixed, sv.w);
+    if (rc) return rc;
+    static thread_local double *pinned = nullptr;
+    if (!pinned) {
+        if (cudaMallocHost(&pinned, sizeof(double) * (8 * DST_MAX_VEC + 16)) != cudaSuccess) {
+            pinned = nullptr;
+            return DST_ERR_OOM;
+        }
+    }
+    sv.w.host = pinned;
+    const int64_t n = mesh->n_unknowns;
+    // b = -D_w21 psi0 and ||b||
+    sv.prof.on = o.profile != 0;
+    if ((rc = sv.run(K_RHS, 1, 16.0 * n + 16.0 * mesh->n_spatial * mesh->nc, 0.0,
+                     [&] { return dst_internal_rhs(mesh, sv.w.b, s); })))
+        return rc;
+    double bnorm;
+    if ((rc = sv.norm(sv.w.b, 1, bnorm))) return rc;
+    if (!std::isfinite(bnorm)) return DST_ERR_NAN;
+    if (!o.use_initial_guess) DST_CUDA_TRY(cudaMemsetAsync(psi, 0, sizeof(double2) * n, s));
+    if (bnorm == 0.0) {
+        DST_CUDA_TRY(cudaMemsetAsync(psi, 0, sizeof(double2) * n, s));
+        DST_CUDA_TRY(cudaStreamSynchronize(s));
+        st.rel_resid_true = 0.0;
+        st.bytes_moved = sv.bytes;
+        return DST_OK;
+    }
+    const double tol = o.rtol * bnorm;
+    double beta = 0.0;
+    if (!mixed) {
+        rc = sv.gmres(DST_FP64, psi, sv.w.b, !o.use_initial_guess, tol, o.max_iters, beta);
+        if (rc) return rc;
+    } else {
+        // r64 = b - A64 x
+        double rnorm;
+        if (!o.use_initial_guess) {
+            DST_CUDA_TRY(cudaMemcpyAsync(sv.w.r64, sv.w.b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
+            rnorm = bnorm;
+        } else {
+            if ((rc = sv.apply(DST_FP64, psi, sv.w.tmp))) return rc;
+            if ((rc = sv.residual(sv.w.b, sv.w.tmp, sv.w.r64, sv.w.nrm + 2))) return rc;
+            DST_CUDA_TRY(cudaMemcpyAsync(sv.w.host, sv.w.nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+            if ((rc = sv.sync())) return rc;
+            rnorm = std::sqrt(sv.w.host[0]);
+        }
+        int refine = 0;
+        while (rnorm > tol && refine < o.max_refine && sv.iters < o.max_iters) {
+            if (!std::isfinite(rnorm)) return DST_ERR_NAN;
+            double inner_beta;
+            DST_CUDA_TRY(cudaMemsetAsync(sv.w.d, 0, sizeof(double2) * n, s));
+            rc = sv.gmres(DST_FP32, sv.w.d, sv.w.r64, true, o.inner_rtol * rnorm, o.max_iters, inner_beta);
+            if (rc) return rc;
+            if ((rc = sv.run(K_MISC, 1, 48.0 * n, 2.0 * n, [&] { return dst_k_axpy1(n, sv.w.d, psi, s); }))) return rc;
+            if ((rc = sv.apply(DST_FP64, psi, sv.w.tmp))) return rc;
+            if ((rc = sv.residual(sv.w.b, sv.w.tmp, sv.w.r64, sv.w.nrm + 2))) return rc;
+            DST_CUDA_TRY(cudaMemcpyAsync(sv.w.host, sv.w.nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+            if ((rc = sv.sync())) return rc;
+            rnorm = std::sqrt(sv.w.host[0]);
+            ++refine;
+        }
+        st.refinements = refine;
+        beta = rnorm;
+    }
+    if ((rc = sv.sync())) return rc;
+    for (int c = 0; c < K_NCLASS; ++c) {
+        st.kernel_ms[c] = sv.prof.ms[c];
+        st.kernel_launches[c] = sv.prof.launches[c];
+        st.kernel_bytes[c] = sv.prof.bytes[c];
+        st.kernel_flops[c] = sv.prof.flops[c];
+        st.launches += sv.prof.launches[c];
+    }
+    st.iters = sv.iters;
+    st.restarts = sv.restarts;
+    st.rel_resid_true = beta / bnorm;
+    st.rel_resid_est = sv.resid_est / bnorm;
+    st.bytes_moved = sv.bytes;
+    if (!std::isfinite(beta)) return DST_ERR_NAN;
+    return beta <= tol ? DST_OK : DST_NOT_CONVERGED;
+}
+
+extern "C" int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, dst_solve_stats *stats,
+                         void *stream) {
+    auto t0 = std::chrono::steady_clock::now();
+    dst_solve_stats st = {};
+    int rc;
+    dst_solve_opts o;
+    dst_default_solve_opts(&o);
+    if (opts) o = *opts;
+    if (!mesh || !psi || o.restart < 1 || o.restart > DST_MAX_VEC - 1 || o.max_iters < 0 || !(o.rtol >= 0) ||
+        (o.mixed_precision && (!(o.inner_rtol > 0) || o.max_refine < 1))) {
+        rc = DST_ERR_ARG;
+    } else if (!mesh->d_psi0) {
+        rc = DST_ERR_STATE;
+    } else {
+        rc = solve_impl(mesh, o, (double2 *)psi, st, (cudaStream_t)stream);
+    }
+    st.status = rc;
+    st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = st;
+    return rc;
+}

@@ -1,0 +1,77 @@
+// Internal declarations of the diracst library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/diracst.h"
+
+#define DST_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) {                             \
+            dst_internal_set_cuda_error(e_, #expr, __FILE__, __LINE__); \
+            return DST_ERR_CUDA;                             \
+        }                                                    \
+    } while (0)
+
+void dst_internal_set_cuda_error(cudaError_t e, const char *expr, const char *file, int line);
+
+// Geometry of one spatial axis, as the kernels see it.
+struct AxisDesc {
+    int64_t n;      // unknown nodes along the axis
+    int64_t nel;    // elements along the axis
+    int bc;         // DST_BC_*
+    int u0;         // geometric index of unknown node 0 (1 for Dirichlet, else 0)
+    double h;       // element size
+};
+
+// Everything an operator-apply kernel needs, passed by value.
+struct OpParams {
+    AxisDesc ax[3];          // x, y, z (unused axes: n = nel = 1, periodic)
+    int64_t nt;              // unknown time layers N_t
+    double ht;               // time element size
+    double m;                // mass
+    int vmode;               // 0: separable (x-only weights), 1: general per-element V
+    const double *wx;        // separable: [2*nel_x]: (m + V_ex) then (-m + V_ex)
+    const double *Vel;       // general: V per spatial element (x fastest)
+};
+
+struct dst_mesh {
+    int device;
+    int d, nc;
+    int64_t nel[3], nt;
+    double lo[4], hi[4];
+    int bc[3];
+    double h[3], ht;
+    int64_t nu[3];
+    int u0[3];
+    int64_t n_spatial, n_unknowns;
+    double m;
+    std::vector<double> V;        // host copy, empty = zero potential
+    bool v_general;               // true if V varies along y or z
+    double *d_wx;                 // [2*nel_x] separable weights
+    double *d_V;                  // general potential (or null)
+    std::vector<double> psi0;     // host copy of the initial layer
+    double2 *d_psi0;              // device copy (null until set)
+    // GMRES workspace (allocated lazily by dst_solve)
+    void *ws;
+    size_t ws_bytes;
+};
+
+OpParams dst_internal_params(const dst_mesh *mesh);
+int dst_internal_update_weights(dst_mesh *mesh);
+
+// Kernel launchers, one translation unit per spatial dimension (apply_d{1,2,3}.cu).
+int dst_launch_apply_d1(const OpParams &p, int precision, const void *x, void *y, cudaStream_t s);
+int dst_launch_apply_d2(const OpParams &p, int precision, const void *x, void *y, cudaStream_t s);
+int dst_launch_apply_d3(const OpParams &p, int precision, const void *x, void *y, cudaStream_t s);
+int dst_launch_rhs_d1(const OpParams &p, const double2 *psi0, double2 *b, cudaStream_t s);
+int dst_launch_rhs_d2(const OpParams &p, const double2 *psi0, double2 *b, cudaStream_t s);
+int dst_launch_rhs_d3(const OpParams &p, const double2 *psi0, double2 *b, cudaStream_t s);
+
+// Dispatch on the mesh dimension.
+int dst_internal_apply(const dst_mesh *mesh, int precision, const void *x, void *y, cudaStream_t s);
+int dst_internal_rhs(const dst_mesh *mesh, double2 *b, cudaStream_t s);

@@ -1,0 +1,236 @@
+// Mesh objects and the C ABI entry points that are not the solver
+// (Algorithm 1 steps 1-5: mesh, initial data, operator, right-hand side).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+static thread_local char g_last_cuda_error[256];
+
+void dst_internal_set_cuda_error(cudaError_t e, const char *expr, const char *file, int line) {
+    snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s failed at %s:%d: %s", expr, file, line,
+             cudaGetErrorString(e));
+}
+
+extern "C" const char *dst_last_error_detail(void) { return g_last_cuda_error; }
+
+extern "C" const char *dst_status_string(int status) {
+    switch (status) {
+        case DST_OK: return "ok";
+        case DST_NOT_CONVERGED: return "not converged (iteration cap reached)";
+        case DST_ERR_ARG: return "invalid argument";
+        case DST_ERR_OOM: return "out of memory";
+        case DST_ERR_CUDA: return "CUDA error";
+        case DST_ERR_NAN: return "non-finite value";
+        case DST_ERR_STATE: return "missing input (initial data not set)";
+        default: return "unknown status";
+    }
+}
+
+OpParams dst_internal_params(const dst_mesh *mesh) {
+    OpParams p;
+    for (int k = 0; k < 3; ++k) {
+        p.ax[k].n = mesh->nu[k];
+        p.ax[k].nel = mesh->nel[k];
+        p.ax[k].bc = mesh->bc[k];
+        p.ax[k].u0 = mesh->u0[k];
+        p.ax[k].h = mesh->h[k];
+    }
+    p.nt = mesh->nt;
+    p.ht = mesh->ht;
+    p.m = mesh->m;
+    p.vmode = mesh->v_general ? 1 : 0;
+    p.wx = mesh->d_wx;
+    p.Vel = mesh->d_V;
+    return p;
+}
+
+// Separable weights (m*beta + V_ex) per x element for beta = +1 and -1.  Only
+// valid when V does not vary along y and z (or is zero).
+int dst_internal_update_weights(dst_mesh *mesh) {
+    const int64_t nx = mesh->nel[0];
+    std::vector<double> w(2 * nx);
+    for (int64_t e = 0; e < nx; ++e) {
+        double v = mesh->V.empty() ? 0.0 : mesh->V[e];
+        w[e] = mesh->m + v;
+        w[nx + e] = -mesh->m + v;
+    }
+    int dev_prev;
+    DST_CUDA_TRY(cudaGetDevice(&dev_prev));
+    DST_CUDA_TRY(cudaSetDevice(mesh->device));
+    cudaError_t e = cudaMemcpy(mesh->d_wx, w.data(), sizeof(double) * 2 * nx, cudaMemcpyHostToDevice);
+    cudaSetDevice(dev_prev);
+    DST_CUDA_TRY(e);
+    return DST_OK;
+}
+
+extern "C" int dst_create_mesh(int d, const int64_t n_el[4], const double lo[4], const double hi[4],
+                               const int bc[3], dst_mesh **out) {
+    if (!out || !n_el || !lo || !hi || !bc) return DST_ERR_ARG;
+    *out = nullptr;
+    if (d < 1 || d > 3) return DST_ERR_ARG;
+    if (n_el[3] < 1 || !(hi[3] > lo[3]) || !std::isfinite(lo[3]) || !std::isfinite(hi[3])) return DST_ERR_ARG;
+    for (int k = 0; k < d; ++k) {
+        if (bc[k] < DST_BC_PERIODIC || bc[k] > DST_BC_DIRICHLET) return DST_ERR_ARG;
+        if (n_el[k] < 1 || (bc[k] == DST_BC_DIRICHLET && n_el[k] < 2)) return DST_ERR_ARG;
+        if (!(hi[k] > lo[k]) || !std::isfinite(lo[k]) || !std::isfinite(hi[k])) return DST_ERR_ARG;
+    }
+    int dev;
+    DST_CUDA_TRY(cudaGetDevice(&dev));
+    dst_mesh *m = new (std::nothrow) dst_mesh();
+    if (!m) return DST_ERR_OOM;
+    m->device = dev;
+    m->d = d;
+    m->nc = d < 3 ? 2 : 4;
+    m->nt = n_el[3];
+    m->lo[3] = lo[3];
+    m->hi[3] = hi[3];
+    m->ht = (hi[3] - lo[3]) / (double)n_el[3];
+    m->n_spatial = 1;
+    for (int k = 0; k < 3; ++k) {
+        if (k < d) {
+            m->nel[k] = n_el[k];
+            m->lo[k] = lo[k];
+            m->hi[k] = hi[k];
+            m->bc[k] = bc[k];
+            m->h[k] = (hi[k] - lo[k]) / (double)n_el[k];
+            if (bc[k] == DST_BC_PERIODIC) { m->nu[k] = n_el[k]; m->u0[k] = 0; }
+            else if (bc[k] == DST_BC_OPEN) { m->nu[k] = n_el[k] + 1; m->u0[k] = 0; }
+            else { m->nu[k] = n_el[k] - 1; m->u0[k] = 1; }
+        } else {
+            m->nel[k] = 1; m->lo[k] = 0; m->hi[k] = 1; m->bc[k] = DST_BC_PERIODIC;
+            m->h[k] = 1.0; m->nu[k] = 1; m->u0[k] = 0;
+        }
+        m->n_spatial *= m->nu[k];
+    }
+    m->n_unknowns = m->n_spatial * m->nt * m->nc;
+    m->m = 1.0;
+    m->v_general = false;
+    m->d_wx = nullptr;
+    m->d_V = nullptr;
+    m->d_psi0 = nullptr;
+    m->ws = nullptr;
+    m->ws_bytes = 0;
+    if (cudaMalloc(&m->d_wx, sizeof(double) * 2 * m->nel[0]) != cudaSuccess) {
+        delete m;
+        return DST_ERR_OOM;
+    }
+    int rc = dst_internal_update_weights(m);
+    if (rc != DST_OK) {
+        dst_destroy_mesh(m);
+        return rc;
+    }
+    *out = m;
+    return DST_OK;
+}
+
+extern "C" int dst_destroy_mesh(dst_mesh *mesh) {
+    if (!mesh) return DST_OK;
+    int dev_prev = 0;
+    cudaGetDevice(&dev_prev);
+    cudaSetDevice(mesh->device);
+    cudaFree(mesh->d_wx);
+    cudaFree(mesh->d_V);
+    cudaFree(mesh->d_psi0);
+    cudaFree(mesh->ws);
+    cudaSetDevice(dev_prev);
+    delete mesh;
+    return DST_OK;
+}
+
+extern "C" int dst_mesh_sizes(const dst_mesh *mesh, int64_t *n_spatial_nodes, int64_t *n_unknowns, int *ncomp) {
+    if (!mesh) return DST_ERR_ARG;
+    if (n_spatial_nodes) *n_spatial_nodes = mesh->n_spatial;
+    if (n_unknowns) *n_unknowns = mesh->n_unknowns;
+    if (ncomp) *ncomp = mesh->nc;
+    return DST_OK;
+}
+
+extern "C" int dst_set_mass(dst_mesh *mesh, double m) {
+    if (!mesh || !std::isfinite(m)) return DST_ERR_ARG;
+    mesh->m = m;
+    return dst_internal_update_weights(mesh);
+}
+
+extern "C" int dst_set_potential(dst_mesh *mesh, const double *V_elem) {
+    if (!mesh) return DST_ERR_ARG;
+    const int64_t nx = mesh->nel[0], nyz = mesh->nel[1] * mesh->nel[2];
+    if (!V_elem) {
+        mesh->V.clear();
+        mesh->v_general = false;
+        return dst_internal_update_weights(mesh);
+    }
+    const int64_t ne = nx * nyz;
+    for (int64_t i = 0; i < ne; ++i)
+        if (!std::isfinite(V_elem[i])) return DST_ERR_ARG;
+    mesh->V.assign(V_elem, V_elem + ne);
+    bool general = false;
+    for (int64_t j = 1; j < nyz && !general; ++j)
+        for (int64_t e = 0; e < nx; ++e)
+            if (V_elem[j * nx + e] != V_elem[e]) { general = true; break; }
+    mesh->v_general = general;
+    if (general) {
+        int dev_prev;
+        DST_CUDA_TRY(cudaGetDevice(&dev_prev));
+        DST_CUDA_TRY(cudaSetDevice(mesh->device));
+        if (!mesh->d_V && cudaMalloc(&mesh->d_V, sizeof(double) * ne) != cudaSuccess) {
+            mesh->d_V = nullptr;
+            cudaSetDevice(dev_prev);
+            return DST_ERR_OOM;
+        }
+        cudaError_t e = cudaMemcpy(mesh->d_V, V_elem, sizeof(double) * ne, cudaMemcpyHostToDevice);
+        cudaSetDevice(dev_prev);
+        DST_CUDA_TRY(e);
+    }
+    return dst_internal_update_weights(mesh);
+}
+
+extern "C" int dst_set_initial_data(dst_mesh *mesh, const double *psi0) {
+    if (!mesh || !psi0) return DST_ERR_ARG;
+    const int64_t n = mesh->n_spatial * mesh->nc * 2;
+    mesh->psi0.assign(psi0, psi0 + n);
+    int dev_prev;
+    DST_CUDA_TRY(cudaGetDevice(&dev_prev));
+    DST_CUDA_TRY(cudaSetDevice(mesh->device));
+    if (!mesh->d_psi0 && cudaMalloc(&mesh->d_psi0, sizeof(double) * n) != cudaSuccess) {
+        mesh->d_psi0 = nullptr;
+        cudaSetDevice(dev_prev);
+        return DST_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpy(mesh->d_psi0, psi0, sizeof(double) * n, cudaMemcpyHostToDevice);
+    cudaSetDevice(dev_prev);
+    DST_CUDA_TRY(e);
+    return DST_OK;
+}
+
+int dst_internal_apply(const dst_mesh *mesh, int precision, const void *x, void *y, cudaStream_t s) {
+    OpParams p = dst_internal_params(mesh);
+    switch (mesh->d) {
+        case 1: return dst_launch_apply_d1(p, precision, x, y, s);
+        case 2: return dst_launch_apply_d2(p, precision, x, y, s);
+        default: return dst_launch_apply_d3(p, precision, x, y, s);
+    }
+}
+
+int dst_internal_rhs(const dst_mesh *mesh, double2 *b, cudaStream_t s) {
+    OpParams p = dst_internal_params(mesh);
+    switch (mesh->d) {
+        case 1: return dst_launch_rhs_d1(p, mesh->d_psi0, b, s);
+        case 2: return dst_launch_rhs_d2(p, mesh->d_psi0, b, s);
+        default: return dst_launch_rhs_d3(p, mesh->d_psi0, b, s);
+    }
+}
+
+extern "C" int dst_apply_operator(const dst_mesh *mesh, int precision, const void *x, void *y, void *stream) {
+    if (!mesh || !x || !y || (precision != DST_FP64 && precision != DST_FP32)) return DST_ERR_ARG;
+    if (x == y) return DST_ERR_ARG;
+    return dst_internal_apply(mesh, precision, x, y, (cudaStream_t)stream);
+}
+
+extern "C" int dst_build_rhs(const dst_mesh *mesh, void *b, void *stream) {
+    if (!mesh || !b) return DST_ERR_ARG;
+    if (!mesh->d_psi0) return DST_ERR_STATE;
+    return dst_internal_rhs(mesh, (double2 *)b, (cudaStream_t)stream);
+}
