@@ -1,7 +1,12 @@
 import os
 import sys
 
-import pytest
+# The oracle's sparse LU and small dense products gain nothing from many BLAS
+# threads; capping them keeps the CPU suite fast on a shared or loaded host.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "2")
+
+import pytest  # noqa: E402
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
