@@ -147,6 +147,31 @@ DST_API int dst_arnoldi_project(int64_t n, int nvec, const void *V, const void *
 DST_API int dst_arnoldi_update(int64_t n, int nvec, const void *V, const void *h, void *w,
                        void *nrm2, void *stream);
 
+/*
+ * dst_arnoldi_project without any device allocation.  The paper has no
+ * counterpart: this call exists for callers that must not allocate device
+ * memory - code that runs under a fixed device-memory budget or inside a host
+ * framework that owns every device allocation itself, and code on a
+ * latency-critical host path where an allocation could stall, fail late or
+ * take a lock the caller already holds.  It computes exactly what
+ * dst_arnoldi_project computes (same kernels, same reduction order, so the
+ * same bits) and the caller still passes V, w and h.
+ *
+ * Scratch: the reduction partials live in one statically sized device array
+ * of the library (1216 x 64 complex doubles = 1,245,184 bytes), which every
+ * GPU that loads the library keeps until the process exits.  Limit:
+ * 1 <= nvec <= 64 (any n >= 1); larger nvec returns DST_ERR_ARG and
+ * dst_last_error_detail() says why.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current
+ * and caches it; make that first call before any stream capture.  No call
+ * allocates or frees memory.  All calls share the one array, which keeps the
+ * last call's contents; each call writes every partial it reads, so nothing
+ * needs clearing, but calls that overlap on the GPU (other streams or host
+ * threads) race on it and must be serialised by the caller.
+ */
+DST_API int dst_arnoldi_project_noalloc(int64_t n, int nvec, const void *V, const void *w, void *h,
+                                        void *stream);
+
 typedef struct {
     int restart;            /* Krylov dimension m of GMRES(m); 1..64, default 30 */
     int max_iters;          /* total Arnoldi steps across restarts (and refinements) */

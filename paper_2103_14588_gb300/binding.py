@@ -25,7 +25,7 @@ EXPORTED = (
     "dst_create_mesh", "dst_destroy_mesh", "dst_mesh_sizes", "dst_set_mass", "dst_set_potential",
     "dst_set_initial_data", "dst_build_rhs", "dst_apply_operator", "dst_arnoldi_project",
     "dst_arnoldi_update", "dst_default_solve_opts", "dst_solve", "dst_status_string",
-    "dst_last_error_detail",
+    "dst_last_error_detail", "dst_arnoldi_project_noalloc",
 )
 
 
@@ -33,7 +33,7 @@ class DstError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
         detail = ""
-        if code == DST_ERR_CUDA and _lib is not None:
+        if code in (DST_ERR_CUDA, DST_ERR_ARG) and _lib is not None:
             detail = ": " + _lib.dst_last_error_detail().decode(errors="replace")
         super().__init__("%s failed with %d (%s)%s" % (where, code, dst_status_string(code), detail))
 
@@ -82,6 +82,7 @@ def _load():
         "dst_apply_operator": (c_int, [vp, c_int, vp, vp, vp]),
         "dst_arnoldi_project": (c_int, [i64, c_int, vp, vp, vp, vp]),
         "dst_arnoldi_update": (c_int, [i64, c_int, vp, vp, vp, vp, vp]),
+        "dst_arnoldi_project_noalloc": (c_int, [i64, c_int, vp, vp, vp, vp]),
         "dst_default_solve_opts": (c_int, [P(dst_solve_opts)]),
         "dst_solve": (c_int, [vp, P(dst_solve_opts), vp, P(dst_solve_stats), vp]),
         "dst_status_string": (ctypes.c_char_p, [c_int]),
@@ -216,6 +217,16 @@ def dst_arnoldi_project(n, nvec, V, w, h, stream=None):
     ph = _dev_ptr(h, torch.complex128, nvec, "h")
     return _check(_lib.dst_arnoldi_project(int(n), int(nvec), pV, pw, ph, _stream(stream, V, w, h)),
                   "dst_arnoldi_project")
+
+
+def dst_arnoldi_project_noalloc(n, nvec, V, w, h, stream=None):
+    """h = V^H w using the library's static scratch instead of allocating (see diracst.h)."""
+    import torch
+    pV = _dev_ptr(V, torch.complex128, n * nvec, "V")
+    pw = _dev_ptr(w, torch.complex128, n, "w")
+    ph = _dev_ptr(h, torch.complex128, nvec, "h")
+    return _check(_lib.dst_arnoldi_project_noalloc(int(n), int(nvec), pV, pw, ph, _stream(stream, V, w, h)),
+                  "dst_arnoldi_project_noalloc")
 
 
 def dst_arnoldi_update(n, nvec, V, h, w, nrm2, stream=None):

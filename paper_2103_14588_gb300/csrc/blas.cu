@@ -6,6 +6,8 @@
 // vector, threads accumulate their elements in a fixed order, warps reduce by
 // a fixed shuffle tree, CTAs write partials that a second kernel sums in CTA
 // order.  All arithmetic of these kernels is FP64.
+#include <mutex>
+
 #include "blas.h"
 
 namespace dst {
@@ -257,6 +259,56 @@ int dst_reduction_blocks(int64_t n) {
     int64_t b = (n + 1023) / 1024;
     if (b > DST_MAX_RED_BLOCKS) b = DST_MAX_RED_BLOCKS;
     return (int)(b < 1 ? 1 : b);
+}
+
+// ---- projection without device allocation --------------------------------
+//
+// Scratch for callers that may not allocate device memory: the reduction
+// partials live in a fixed file-scope device array instead of coming from the
+// stream-ordered allocator.  Host code cannot pass the symbol itself (on the
+// host it only names a shadow variable); its device address is looked up once
+// per device with cudaGetSymbolAddress and cached.
+#define DST_NOALLOC_PARTIALS ((size_t)DST_MAX_RED_BLOCKS * DST_MAX_VEC)
+static __device__ __align__(256) double2 g_noalloc_partials[DST_NOALLOC_PARTIALS];
+
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_addr[DST_MAX_DEVICES];
+
+static int noalloc_scratch(void **out) {
+    int dev = 0;
+    DST_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= DST_MAX_DEVICES) {
+        dst_internal_set_error_detail("dst_arnoldi_project_noalloc: device ordinal out of range");
+        return DST_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        DST_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_partials));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return DST_OK;
+}
+
+extern "C" int dst_arnoldi_project_noalloc(int64_t n, int nvec, const void *V, const void *w, void *h,
+                                           void *stream) {
+    if (n < 1 || !V || !w || !h) return DST_ERR_ARG;
+    if (nvec < 1 || nvec > DST_MAX_VEC) {
+        dst_internal_set_error_detail("dst_arnoldi_project_noalloc: nvec must be 1..64 (the static scratch "
+                                      "holds 1216 x 64 partial sums)");
+        return DST_ERR_ARG;
+    }
+    const int nblk = dst_reduction_blocks(n);
+    if ((size_t)nblk * (size_t)nvec > DST_NOALLOC_PARTIALS) {
+        dst_internal_set_error_detail("dst_arnoldi_project_noalloc: partial sums exceed the static scratch");
+        return DST_ERR_ARG;
+    }
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != DST_OK) return rc;
+    return dst_k_project(n, nvec, (const double2 *)V, (const double2 *)w, (double2 *)h, (double2 *)scratch,
+                         nblk, (cudaStream_t)stream);
 }
 
 // ---- C ABI wrappers -------------------------------------------------------

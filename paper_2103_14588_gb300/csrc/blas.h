@@ -5,6 +5,7 @@
 
 #define DST_MAX_VEC 64            // basis vectors one projection / update handles
 #define DST_MAX_RED_BLOCKS 1216   // CTAs of a reduction pass (8 per SM)
+#define DST_MAX_DEVICES 64        // device ordinals the static-scratch entry point tracks
 
 int dst_reduction_blocks(int64_t n);
 int dst_k_project(int64_t n, int nvec, const double2 *V, const double2 *w, double2 *h, double2 *partials,

@@ -18,6 +18,7 @@
     } while (0)
 
 void dst_internal_set_cuda_error(cudaError_t e, const char *expr, const char *file, int line);
+void dst_internal_set_error_detail(const char *msg);
 
 // Geometry of one spatial axis, as the kernels see it.
 struct AxisDesc {

@@ -14,6 +14,10 @@ void dst_internal_set_cuda_error(cudaError_t e, const char *expr, const char *fi
              cudaGetErrorString(e));
 }
 
+void dst_internal_set_error_detail(const char *msg) {
+    snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s", msg);
+}
+
 extern "C" const char *dst_last_error_detail(void) { return g_last_cuda_error; }
 
 extern "C" const char *dst_status_string(int status) {
