@@ -124,7 +124,8 @@ DST_API int dst_build_rhs(const dst_mesh *mesh, void *b, void *stream);
  * Sec. 2.2 evaluated as a sum-factorised stencil), x and y DEVICE vectors of
  * n_unknowns complex values in the given precision (DST_FP64: double pairs,
  * DST_FP32: float pairs, arithmetic in that precision).  x and y must not
- * overlap.  Errors: DST_ERR_ARG, DST_ERR_CUDA.
+ * overlap and must be 16-byte aligned (every cudaMalloc / PyTorch allocation
+ * is).  Errors: DST_ERR_ARG, DST_ERR_CUDA.
  */
 DST_API int dst_apply_operator(const dst_mesh *mesh, int precision, const void *x, void *y,
                        void *stream);
@@ -182,6 +183,15 @@ typedef struct {
     int max_refine;         /* cap on refinement steps (mixed only) */
     int use_initial_guess;  /* 1: psi holds x0 on entry; 0: start from zero */
     int profile;            /* 1: time every kernel class with CUDA events (small overhead) */
+    int inner_cycles;       /* GMRES(m) cycles per refinement step (mixed only; 0 = until
+                               inner_rtol), default 1 */
+    int ortho;              /* Gram-Schmidt: 0 = classical, second pass only when the DGKS test
+                               asks (norm fell below 1/sqrt 2 of its value before the pass);
+                               1 = always two classical passes (CGS2) */
+    int mixed_ortho;        /* mixed only: arithmetic of the inner Gram-Schmidt.  0 = double-FP32
+                               (basis stored as FP32 hi/lo planes, 48-bit significand, error-free
+                               FP32 products and sums, FP64 reductions; needs inner_cycles = 1),
+                               1 = native FP64 (FP64 basis) */
 } dst_solve_opts;
 
 /* Kernel classes of dst_solve_stats' per-class arrays. */
@@ -207,6 +217,7 @@ typedef struct {
     double seconds;         /* host wall time of the call (includes synchronisation) */
     double bytes_moved;     /* algorithmic device bytes of the kernels launched */
     double launches;        /* kernel launches of the call */
+    int reorths;            /* Arnoldi steps that took a second Gram-Schmidt pass */
     double kernel_ms[8];        /* device time per DST_K_* class (opts.profile only, else 0) */
     double kernel_launches[8];  /* kernel launches per class */
     double kernel_bytes[8];     /* algorithmic bytes per class (reads + writes) */
@@ -214,7 +225,9 @@ typedef struct {
 } dst_solve_stats;
 
 /* Fill opts with the defaults (restart 30, max_iters 100000, rtol 1e-8,
- * FP64, inner_rtol 1e-4, max_refine 50, zero initial guess, no profiling). */
+ * FP64, inner_rtol 1e-4, max_refine 100000, zero initial guess, no
+ * profiling, one inner cycle per refinement, selective reorthogonalisation,
+ * double-FP32 inner Gram-Schmidt). */
 DST_API int dst_default_solve_opts(dst_solve_opts *opts);
 
 /*

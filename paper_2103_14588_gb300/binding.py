@@ -42,14 +42,15 @@ class dst_solve_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("mixed_precision", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("ortho", ctypes.c_int),
+                ("mixed_ortho", ctypes.c_int)]
 
 
 class dst_solve_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("status", ctypes.c_int), ("rel_resid_true", ctypes.c_double),
                 ("rel_resid_est", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("bytes_moved", ctypes.c_double), ("launches", ctypes.c_double),
+                ("bytes_moved", ctypes.c_double), ("launches", ctypes.c_double), ("reorths", ctypes.c_int),
                 ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_double * 8),
                 ("kernel_bytes", ctypes.c_double * 8), ("kernel_flops", ctypes.c_double * 8)]
 

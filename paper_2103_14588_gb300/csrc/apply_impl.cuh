@@ -132,7 +132,7 @@ __device__ __forceinline__ void node_coef(const OpParams &p, int64_t ix, int64_t
     if (D >= 2) nc.cy = axis_coef<T>(p.ax[1], iy);
     if (D >= 3) nc.cz = axis_coef<T>(p.ax[2], iz);
     const int64_t nelx = p.ax[0].nel;
-    if (p.vmode == 0) {
+    if (p.vmode != 1) {
         for (int s = 0; s < 2; ++s) {
             nc.wl[s] = nc.cx.eL ? (T)p.wx[s * nelx + nc.cx.eL_idx] : (T)0;
             nc.wr[s] = nc.cx.eR ? (T)p.wx[s * nelx + nc.cx.eR_idx] : (T)0;
@@ -300,7 +300,7 @@ apply_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typename C2
 
     NodeCoef<D, T> k;
     if (valid) node_coef<D, T>(p, ix, iy, iz, k);
-    const bool vgen = p.vmode != 0;
+    const bool vgen = p.vmode == 1;
     const T h6 = (T)(p.ht / 6.0);
 
     V accP[NC], accC[NC];
@@ -367,7 +367,7 @@ rhs_kernel(OpParams p, const double2 *__restrict__ psi0, double2 *__restrict__ b
     NodeCoef<D, double> k;
     node_coef<D, double>(p, ix, iy, iz, k);
     V GC[NC], GM[NC];
-    spatial_G<D, NC, double, S::BX, S::BY>(box, tx + 1, D >= 2 ? ty + 1 : 0, D >= 3 ? tz + 1 : 0, k, p.vmode != 0, GC, GM);
+    spatial_G<D, NC, double, S::BX, S::BY>(box, tx + 1, D >= 2 ? ty + 1 : 0, D >= 3 ? tz + 1 : 0, k, p.vmode == 1, GC, GM);
     const double h6 = p.ht / 6.0;
     V *dst = b + ((iz * ny + iy) * nx + ix) * NC;
 #pragma unroll

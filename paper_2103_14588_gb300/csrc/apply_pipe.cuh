@@ -1,0 +1,370 @@
+// Pipelined operator apply: time planes staged through a shared-memory ring
+// by asynchronous copies (cp.async, L2 -> shared, zero-filled outside
+// non-periodic boundaries), several planes in flight per CTA.
+//
+// Same operator and evaluation order as apply_impl.cuh: per time plane the
+// spatial sum-factorised fields of Appendix A's element matrices
+// (D^0 = (x)M, D^k = C on axis k, M elsewhere) combined with the spin matrices
+// into G_C (partner of the time convection C_t) and G_M (partner of the time
+// mass M_t), then the two time stencils through two running accumulators per
+// output.  One CTA owns a spatial tile (one output node per thread) and a
+// chunk of time layers; it walks the chunk's planes plus one halo plane on
+// each side.  Each plane of the tile + spatial halo is copied once into the
+// ring; every thread then reads its 3^d neighbourhood from shared memory.
+// One barrier per plane: after it, the slot consumed one plane earlier is
+// free and the copies of the next-but-(S-1) plane are issued into it.
+#pragma once
+
+#include "apply_fast.cuh"
+
+#define DST_MAX_DEVICES_APPLY 64
+
+namespace dst {
+
+template <int D> struct PipeTile;
+template <> struct PipeTile<1> { static constexpr int TX = 256, TY = 1, TZ = 1, TT = 32; };
+template <> struct PipeTile<2> { static constexpr int TX = 32, TY = 8, TZ = 1, TT = 8; };
+template <> struct PipeTile<3> { static constexpr int TX = 16, TY = 4, TZ = 4, TT = 8; };
+
+template <int D, int NC, typename T>
+struct PipeShape {
+    using Tile = PipeTile<D>;
+    static constexpr int BX = Tile::TX + 2;
+    static constexpr int BY = D >= 2 ? Tile::TY + 2 : 1;
+    static constexpr int BZ = D >= 3 ? Tile::TZ + 2 : 1;
+    static constexpr int BOX = BX * BY * BZ;                          // nodes per staged plane
+    static constexpr int NODE_BYTES = NC * 2 * (int)sizeof(T);        // 16, 32 or 64
+    static constexpr int CHUNKS = NODE_BYTES / 16;                    // 16-byte copies per node
+    static constexpr int NTHR = Tile::TX * Tile::TY * Tile::TZ;
+    static constexpr int STAGES = (BOX * NODE_BYTES * 4 <= 96 * 1024) ? 4 : 3;
+    static constexpr int SMEM = STAGES * BOX * NODE_BYTES;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool ok) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = ok ? 16 : 0;     // n = 0: nothing read, 16 zero bytes written
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// The 16-byte copies one thread issues for every plane: source byte offset
+// within a time layer (-1: outside a non-periodic boundary, zero-filled) and
+// destination byte offset within a ring slot.  Computed once per thread, so
+// the plane loop does no index arithmetic (periodic wrap needs 64-bit modulo).
+template <int D, int NC, typename T>
+struct CopyPlan {
+    static constexpr int PER_THREAD =
+        (PipeShape<D, NC, T>::BOX * PipeShape<D, NC, T>::CHUNKS + PipeShape<D, NC, T>::NTHR - 1) /
+        PipeShape<D, NC, T>::NTHR;
+    int src[PER_THREAD];
+    int dst[PER_THREAD];
+};
+
+template <int D, int NC, typename T>
+__device__ __forceinline__ void make_copy_plan(const OpParams &p, int64_t x0, int64_t y0, int64_t z0,
+                                               CopyPlan<D, NC, T> &cp) {
+    using S = PipeShape<D, NC, T>;
+    const int64_t nx = p.ax[0].n, ny = p.ax[1].n;
+#pragma unroll
+    for (int j = 0; j < CopyPlan<D, NC, T>::PER_THREAD; ++j) {
+        const int i = threadIdx.x + j * S::NTHR;
+        cp.dst[j] = -1;
+        cp.src[j] = -1;
+        if (i >= S::BOX * S::CHUNKS) continue;
+        const int node = i / S::CHUNKS, part = i % S::CHUNKS;
+        const int bx = node % S::BX, by = (node / S::BX) % S::BY, bz = node / (S::BX * S::BY);
+        const int64_t gx = axis_nbr(p.ax[0], x0 - 1 + bx);
+        const int64_t gy = D >= 2 ? axis_nbr(p.ax[1], y0 - 1 + by) : 0;
+        const int64_t gz = D >= 3 ? axis_nbr(p.ax[2], z0 - 1 + bz) : 0;
+        cp.dst[j] = node * S::NODE_BYTES + part * 16;
+        if (gx >= 0 && gy >= 0 && gz >= 0) cp.src[j] = (int)(((gz * ny + gy) * nx + gx) * S::NODE_BYTES + part * 16);
+    }
+}
+
+// Issue the copies of one plane (tile box, one-node halo) into a ring slot.
+template <int D, int NC, typename T>
+__device__ __forceinline__ void issue_plane(const CopyPlan<D, NC, T> &cp, const char *layer, char *slot) {
+#pragma unroll
+    for (int j = 0; j < CopyPlan<D, NC, T>::PER_THREAD; ++j)
+        if (cp.dst[j] >= 0) cp_async16(slot + cp.dst[j], layer + (cp.src[j] >= 0 ? cp.src[j] : 0), cp.src[j] >= 0);
+}
+
+template <int NC, typename T>
+__device__ __forceinline__ NodeV<NC, T> smem_node(const char *slot, int node) {
+    NodeV<NC, T> v;
+    if (sizeof(T) == 4) {
+        const float4 *q = reinterpret_cast<const float4 *>(slot + (size_t)node * NC * 8);
+#pragma unroll
+        for (int k = 0; k < NC / 2; ++k) {
+            const float4 f = q[k];
+            v.c[2 * k].x = f.x; v.c[2 * k].y = f.y; v.c[2 * k + 1].x = f.z; v.c[2 * k + 1].y = f.w;
+        }
+    } else {
+        const double2 *q = reinterpret_cast<const double2 *>(slot + (size_t)node * NC * 16);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { const double2 f = q[c]; v.c[c].x = f.x; v.c[c].y = f.y; }
+    }
+    return v;
+}
+
+// Per-kernel constants of the standard interior stencils.  With
+// M = h/6 [1,4,1] and C = 1/2 [-1,0,1] on every axis, the spatial fields are
+// unscaled [1,4,1] / [-1,0,1] sums times fixed factors; those factors, the 1/2
+// and h_t/6 of the time stencils and the mass m are folded into these
+// constants, so G_C' = G_C / 2 and G_M' = (h_t/6) G_M come out directly.
+template <typename T>
+struct StdConst {
+    T kc;        // G_C' = i kc PM                      (kc = 1/2 prod h_k/6)
+    T km;        // mass part of G_M': -beta m km PM    (km = (h_t/6) prod h_k/6)
+    T ka[3];     // alpha_k part of G_M': i ka[k] alpha_k PC_k  (ka = (h_t/6) 1/2 prod_{j!=k} h_j/6)
+};
+
+template <int D, typename T>
+__host__ __device__ inline StdConst<T> std_const(const OpParams &p) {
+    StdConst<T> c;
+    double pm = 1.0;
+    for (int k = 0; k < D; ++k) pm *= p.ax[k].h / 6.0;
+    const double ht6 = p.ht / 6.0;
+    c.kc = (T)(0.5 * pm);
+    c.km = (T)(ht6 * pm);
+    for (int k = 0; k < 3; ++k) {
+        double q = 0.5 * ht6;
+        for (int j = 0; j < D; ++j)
+            if (j != k) q *= p.ax[j].h / 6.0;
+        c.ka[k] = (T)q;
+    }
+    return c;
+}
+
+// i s (alpha_k P)[c] accumulated into G (NC = 2: alpha = (sigma_x, sigma_y);
+// NC = 4: alpha_k = [[0, sigma_k], [sigma_k, 0]]).
+template <int NC, typename V, typename T>
+__device__ __forceinline__ void add_i_alpha(int k, T s, const V *P, V *G) {
+    // i * (a.x + i a.y) * s = (-s a.y, s a.x)
+    auto addi = [&](V &g, V a, T f) { g.x = fma(-f, a.y, g.x); g.y = fma(f, a.x, g.y); };
+    if (NC == 2) {
+        if (k == 0) { addi(G[0], P[1], s); addi(G[1], P[0], s); }
+        else {      // sigma_y: (-i b, i a): i*(-i b) = b, i*(i a) = -a
+            G[0].x = fma(s, P[1].x, G[0].x); G[0].y = fma(s, P[1].y, G[0].y);
+            G[1].x = fma(-s, P[0].x, G[1].x); G[1].y = fma(-s, P[0].y, G[1].y);
+        }
+    } else {
+        if (k == 0) { addi(G[0], P[3], s); addi(G[1], P[2], s); addi(G[2], P[1], s); addi(G[3], P[0], s); }
+        else if (k == 1) {
+            G[0].x = fma(s, P[3].x, G[0].x); G[0].y = fma(s, P[3].y, G[0].y);
+            G[1].x = fma(-s, P[2].x, G[1].x); G[1].y = fma(-s, P[2].y, G[1].y);
+            G[2].x = fma(s, P[1].x, G[2].x); G[2].y = fma(s, P[1].y, G[2].y);
+            G[3].x = fma(-s, P[0].x, G[3].x); G[3].y = fma(-s, P[0].y, G[3].y);
+        } else {    // sigma_z: (a, -b)
+            addi(G[0], P[2], s); addi(G[1], P[3], -s); addi(G[2], P[0], s); addi(G[3], P[1], -s);
+        }
+    }
+}
+
+// G_C' and G_M' of a node whose stencils are the standard interior ones.
+// WV: x-only potential weights (w = m beta + V per x element) instead of m beta.
+template <int D, int NC, typename T, bool WV, typename Get>
+__device__ __forceinline__ void fields_std(Get get, const StdConst<T> &sc, T m, const T (&wx)[2][3],
+                                           typename C2<T>::type *GC, typename C2<T>::type *GM) {
+    using V = typename C2<T>::type;
+    const int NZ = D >= 3 ? 3 : 1, NY = D >= 2 ? 3 : 1;
+    V QM[NC], QCx[NC], QCy[NC], QCz[NC], QW[NC];   // sums over z of [1,4,1] (and [-1,0,1] for z)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { QM[c] = cz<V>(); QCx[c] = cz<V>(); QCy[c] = cz<V>(); QCz[c] = cz<V>(); QW[c] = cz<V>(); }
+#pragma unroll (D >= 3 ? 1 : 3)
+    for (int dz = 0; dz < NZ; ++dz) {
+        V PM[NC], PCx[NC], PCy[NC], PW[NC];
+#pragma unroll
+        for (int dy = 0; dy < NY; ++dy) {
+            const int r = (dz * NY + dy) * 3;
+            const NodeV<NC, T> n0 = get(r), n1 = get(r + 1), n2 = get(r + 2);
+            const T wy = (D >= 2 && dy == 1) ? (T)4 : (T)1;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const V x0 = n0.c[c], x1 = n1.c[c], x2 = n2.c[c];
+                V rM, rC, rW;
+                rM.x = fma((T)4, x1.x, x0.x + x2.x); rM.y = fma((T)4, x1.y, x0.y + x2.y);
+                rC.x = x2.x - x0.x; rC.y = x2.y - x0.y;
+                if (WV) {
+                    const int sb = Beta<D>::s(c) > 0 ? 0 : 1;
+                    rW = cfma_r(wx[sb][0], x0, cfma_r(wx[sb][1], x1, cmul_r(wx[sb][2], x2)));
+                }
+                if (dy == 0) {
+                    PM[c] = rM; PCx[c] = rC; if (WV) PW[c] = rW;
+                    if (D >= 2) { PCy[c].x = -rM.x; PCy[c].y = -rM.y; }
+                } else {
+                    PM[c] = cfma_r(wy, rM, PM[c]);
+                    PCx[c] = cfma_r(wy, rC, PCx[c]);
+                    if (WV) PW[c] = cfma_r(wy, rW, PW[c]);
+                    if (D >= 2 && dy == 2) PCy[c] = cadd(PCy[c], rM);
+                }
+            }
+        }
+        const T wz = (D >= 3 && dz == 1) ? (T)4 : (T)1;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            QM[c] = cfma_r(wz, PM[c], QM[c]);
+            QCx[c] = cfma_r(wz, PCx[c], QCx[c]);
+            if (WV) QW[c] = cfma_r(wz, PW[c], QW[c]);
+            if (D >= 2) QCy[c] = cfma_r(wz, PCy[c], QCy[c]);
+            if (D >= 3) {
+                if (dz == 0) QCz[c] = cmul_r((T)(-1), PM[c]);
+                else if (dz == 2) QCz[c] = cadd(QCz[c], PM[c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        GC[c].x = -sc.kc * QM[c].y; GC[c].y = sc.kc * QM[c].x;             // i kc QM
+        if (WV) {
+            GM[c] = cmul_r(-sc.km, QW[c]);                                   // weights carry m beta + V
+        } else {
+            const T f = Beta<D>::s(c) > 0 ? -m * sc.km : m * sc.km;          // -beta m km
+            GM[c] = cmul_r(f, QM[c]);
+        }
+    }
+    add_i_alpha<NC>(0, sc.ka[0], QCx, GM);
+    if (D >= 2) add_i_alpha<NC>(1, sc.ka[1], QCy, GM);
+    if (D >= 3) add_i_alpha<NC>(2, sc.ka[2], QCz, GM);
+}
+
+template <int D, int NC, typename T, bool NOV>
+__global__ void __launch_bounds__(PipeShape<D, NC, T>::NTHR)
+apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typename C2<T>::type *__restrict__ y,
+                  int64_t tiles_x, int64_t tiles_y) {
+    using V = typename C2<T>::type;
+    using S = PipeShape<D, NC, T>;
+    using Tile = typename S::Tile;
+    extern __shared__ __align__(16) char ring[];
+
+    const int64_t tile = blockIdx.x;
+    const int64_t chunk = blockIdx.y;
+    const int64_t x0 = (tile % tiles_x) * Tile::TX;
+    const int64_t y0 = ((tile / tiles_x) % tiles_y) * Tile::TY;
+    const int64_t z0 = (tile / (tiles_x * tiles_y)) * Tile::TZ;
+    const int tx = threadIdx.x % Tile::TX;
+    const int ty = (threadIdx.x / Tile::TX) % Tile::TY;
+    const int tz = threadIdx.x / (Tile::TX * Tile::TY);
+    const int64_t ix = x0 + tx, iy = y0 + ty, iz = z0 + tz;
+    const int64_t nx = p.ax[0].n, ny = p.ax[1].n, nz = p.ax[2].n;
+    const bool valid = ix < nx && iy < ny && iz < nz;
+    const int64_t N = p.nt;
+    const int64_t t0 = 1 + chunk * Tile::TT;
+    const int64_t t1 = min(t0 + (int64_t)Tile::TT, N + 1);
+    const int64_t plane_elems = nx * ny * nz * NC;
+    const int64_t self = (iz * ny + iy) * nx + ix;
+    const int nplanes = (int)(t1 - t0 + 2);            // planes t0-1 .. t1
+    const int64_t pfirst = t0 - 1;
+
+    NodeCoef<D, T> k;
+    if (valid) node_coef<D, T>(p, ix, iy, iz, k);
+    // standard interior stencils on every axis (periodic / Dirichlet axes, and
+    // open axes away from their two end nodes)
+    bool stdn = valid;
+    if (valid) {
+        stdn = k.cx.eL && k.cx.eR;
+        if (D >= 2) stdn = stdn && k.cy.eL && k.cy.eR;
+        if (D >= 3) stdn = stdn && k.cz.eL && k.cz.eR;
+    }
+    const StdConst<T> sc = std_const<D, T>(p);
+    T wxs[2][3];     // x weights (m beta + V) of the standard path, h_x / 6 folded into StdConst
+    for (int sb = 0; sb < 2; ++sb) {
+        const T wl = valid ? k.wl[sb] : (T)0, wr = valid ? k.wr[sb] : (T)0;
+        wxs[sb][0] = wl; wxs[sb][1] = 2 * (wl + wr); wxs[sb][2] = wr;
+    }
+    CopyPlan<D, NC, T> cplan;
+    make_copy_plan<D, NC, T>(p, x0, y0, z0, cplan);
+    const T h6 = (T)(p.ht / 6.0);
+    const int NY = D >= 2 ? 3 : 1;
+    const int c0 = (tz * S::BY + ty) * S::BX + tx;      // box index of the (-1,-1,-1) neighbour
+
+    auto issue = [&](int i) {
+        const int64_t pl = pfirst + i;
+        if (pl >= 1 && pl <= N)
+            issue_plane<D, NC, T>(cplan, reinterpret_cast<const char *>(x + (pl - 1) * plane_elems),
+                                  ring + (size_t)(i % S::STAGES) * S::BOX * S::NODE_BYTES);
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int i = 0; i < S::STAGES - 1; ++i)
+        if (i < nplanes) issue(i); else cp_async_commit();
+
+    V accP[NC], accC[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { accP[c] = cz<V>(); accC[c] = cz<V>(); }
+
+    for (int i = 0; i < nplanes; ++i) {
+        cp_async_wait<S::STAGES - 2>();
+        __syncthreads();
+        if (i + S::STAGES - 1 < nplanes) issue(i + S::STAGES - 1); else cp_async_commit();
+        const int64_t pl = pfirst + i;
+        const bool have = pl >= 1 && pl <= N;
+        // G_C' = G_C / 2 and G_M' = (h_t / 6) G_M of this plane
+        V GC[NC], GM[NC];
+        if (have && valid) {
+            const char *slot = ring + (size_t)(i % S::STAGES) * S::BOX * S::NODE_BYTES;
+            auto get = [&](int r) {
+                const int dz = r / (3 * NY), dy = (r / 3) % NY, dx = r % 3;
+                return smem_node<NC, T>(slot, c0 + (dz * S::BY + dy) * S::BX + dx);
+            };
+            if (stdn) {
+                fields_std<D, NC, T, !NOV>(get, sc, (T)p.m, wxs, GC, GM);
+            } else {
+                if (NOV) fields_nov<D, NC, T>(get, k, (T)p.m, GC, GM);
+                else fields<D, NC, T>(get, k, GC, GM);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) { GC[c] = cmul_r((T)0.5, GC[c]); GM[c] = cmul_r(h6, GM[c]); }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) { GC[c] = cz<V>(); GM[c] = cz<V>(); }
+        }
+        // y(pl-1) += G_C' + G_M'; y(pl) += (pl < N ? 4 G_M' : G_C' + 2 G_M'); y(pl+1) = G_M' - G_C'
+        const bool last = pl >= N;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            accP[c] = cadd(accP[c], cadd(GC[c], GM[c]));
+            if (last) accC[c] = cadd(accC[c], cfma_r((T)2, GM[c], GC[c]));
+            else accC[c] = cfma_r((T)4, GM[c], accC[c]);
+        }
+        if (valid && pl - 1 >= t0 && pl - 1 < t1) store_node<NC, T>(y + (pl - 2) * plane_elems, self, accP);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            accP[c] = accC[c];
+            accC[c] = csub(GM[c], GC[c]);
+        }
+    }
+    cp_async_wait<0>();
+}
+
+template <int D, int NC, typename T>
+int launch_apply_pipe(const OpParams &p, const typename C2<T>::type *x, typename C2<T>::type *y, cudaStream_t s) {
+    using S = PipeShape<D, NC, T>;
+    using Tile = PipeTile<D>;
+    const int64_t tx = (p.ax[0].n + Tile::TX - 1) / Tile::TX;
+    const int64_t ty = (p.ax[1].n + Tile::TY - 1) / Tile::TY;
+    const int64_t tz = (p.ax[2].n + Tile::TZ - 1) / Tile::TZ;
+    const int64_t chunks = (p.nt + Tile::TT - 1) / Tile::TT;
+    const int64_t tiles = tx * ty * tz;
+    if (tiles <= 0 || tiles > 0x7fffffffLL || chunks > 65535) return DST_ERR_ARG;
+    // byte offsets within one time layer are kept in 32 bits
+    if (p.ax[0].n * p.ax[1].n * p.ax[2].n * S::NODE_BYTES >= (1LL << 31)) return launch_apply<D, NC, T>(p, x, y, s);
+    dim3 grid((unsigned)tiles, (unsigned)chunks);
+    // the shared-memory opt-in is a per-device function attribute: set it once per device
+    static bool configured[2][DST_MAX_DEVICES_APPLY] = {};
+    int dev = 0;
+    DST_CUDA_TRY(cudaGetDevice(&dev));
+    const int nov = p.vmode == 2 ? 1 : 0;
+    auto kern = nov ? apply_pipe_kernel<D, NC, T, true> : apply_pipe_kernel<D, NC, T, false>;
+    if (dev < 0 || dev >= DST_MAX_DEVICES_APPLY || !configured[nov][dev]) {
+        DST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
+        if (dev >= 0 && dev < DST_MAX_DEVICES_APPLY) configured[nov][dev] = true;
+    }
+    kern<<<grid, S::NTHR, S::SMEM, s>>>(p, x, y, tx, ty);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+}  // namespace dst

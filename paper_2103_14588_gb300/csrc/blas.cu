@@ -40,13 +40,20 @@ __device__ __forceinline__ void slice(int64_t n, int64_t &b, int64_t &e) {
     e = b + per < n ? b + per : n;
 }
 
-// partials[blk * nvec + j] = sum over the CTA's slice of conj(V_j) w.
+// partials[blk * nvec + j] = sum over the CTA's slice of conj(V_j) w, and
+// (if wnrm_partials) partials of ||w||^2.  Threads accumulate PROJ_GROUP basis
+// vectors at a time over their elements; each group is reduced across the warp
+// by shuffles and parked in shared memory; one barrier at the end, then the
+// warps' values are summed in warp order.
 __global__ void __launch_bounds__(RED_THREADS)
 project_partial_kernel(int64_t n, int nvec, const double2 *__restrict__ V, const double2 *__restrict__ w,
-                       double2 *__restrict__ partials) {
-    __shared__ double sh[RED_THREADS / 32];
+                       double2 *__restrict__ partials, double *__restrict__ wnrm_partials) {
+    constexpr int NW = RED_THREADS / 32;
+    __shared__ double red[NW][2 * DST_MAX_VEC + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int64_t b, e;
     slice(n, b, e);
+    double wn = 0.0;
     for (int j0 = 0; j0 < nvec; j0 += PROJ_GROUP) {
         const int gv = nvec - j0 < PROJ_GROUP ? nvec - j0 : PROJ_GROUP;
         double ar[PROJ_GROUP], ai[PROJ_GROUP];
@@ -54,6 +61,7 @@ project_partial_kernel(int64_t n, int nvec, const double2 *__restrict__ V, const
         for (int g = 0; g < PROJ_GROUP; ++g) { ar[g] = 0.0; ai[g] = 0.0; }
         for (int64_t i = b + threadIdx.x; i < e; i += RED_THREADS) {
             const double2 wi = w[i];
+            if (j0 == 0) wn = fma(wi.x, wi.x, fma(wi.y, wi.y, wn));
 #pragma unroll
             for (int g = 0; g < PROJ_GROUP; ++g) {
                 if (g < gv) {
@@ -66,11 +74,25 @@ project_partial_kernel(int64_t n, int nvec, const double2 *__restrict__ V, const
 #pragma unroll
         for (int g = 0; g < PROJ_GROUP; ++g) {
             if (g < gv) {
-                double sr = block_sum(ar[g], sh);
-                double si = block_sum(ai[g], sh);
-                if (threadIdx.x == 0) partials[(int64_t)blockIdx.x * nvec + j0 + g] = make_double2(sr, si);
+                const double sr = warp_sum(ar[g]), si = warp_sum(ai[g]);
+                if (lane == 0) { red[warp][2 * (j0 + g)] = sr; red[warp][2 * (j0 + g) + 1] = si; }
             }
         }
+    }
+    wn = warp_sum(wn);
+    if (lane == 0) red[warp][2 * DST_MAX_VEC] = wn;
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * nvec; q += RED_THREADS) {
+        double s_ = 0.0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) s_ += red[k][q];
+        reinterpret_cast<double *>(partials + (int64_t)blockIdx.x * nvec)[q] = s_;
+    }
+    if (wnrm_partials && threadIdx.x == 0) {
+        double s_ = 0.0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) s_ += red[k][2 * DST_MAX_VEC];
+        wnrm_partials[blockIdx.x] = s_;
     }
 }
 
@@ -201,9 +223,22 @@ static unsigned stream_blocks(int64_t n) {
 }
 
 int dst_k_project(int64_t n, int nvec, const double2 *V, const double2 *w, double2 *h, double2 *partials,
-                  int nblk, cudaStream_t s) {
-    project_partial_kernel<<<nblk, RED_THREADS, 0, s>>>(n, nvec, V, w, partials);
+                  int nblk, cudaStream_t s, double *wnrm2, double *wnrm_partials) {
+    project_partial_kernel<<<nblk, RED_THREADS, 0, s>>>(n, nvec, V, w, partials, wnrm2 ? wnrm_partials : nullptr);
     reduce_partials_kernel<<<nvec, RED_THREADS, 0, s>>>(nblk, nvec, partials, h);
+    if (wnrm2) reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, wnrm_partials, wnrm2);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_reduce_partials(int nblk, int nvec, const double2 *partials, double2 *out, cudaStream_t s) {
+    reduce_partials_kernel<<<nvec, RED_THREADS, 0, s>>>(nblk, nvec, partials, out);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_reduce_real(int nblk, const double *partials, double *out, cudaStream_t s) {
+    reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, out);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
@@ -256,7 +291,7 @@ int dst_k_axpy1(int64_t n, const double2 *d, double2 *x, cudaStream_t s) {
 }
 
 int dst_reduction_blocks(int64_t n) {
-    int64_t b = (n + 1023) / 1024;
+    int64_t b = (n + 4095) / 4096;
     if (b > DST_MAX_RED_BLOCKS) b = DST_MAX_RED_BLOCKS;
     return (int)(b < 1 ? 1 : b);
 }
@@ -268,7 +303,7 @@ int dst_reduction_blocks(int64_t n) {
 // stream-ordered allocator.  Host code cannot pass the symbol itself (on the
 // host it only names a shadow variable); its device address is looked up once
 // per device with cudaGetSymbolAddress and cached.
-#define DST_NOALLOC_PARTIALS ((size_t)DST_MAX_RED_BLOCKS * DST_MAX_VEC)
+#define DST_NOALLOC_PARTIALS ((size_t)1216 * DST_MAX_VEC)   // >= DST_MAX_RED_BLOCKS * DST_MAX_VEC
 static __device__ __align__(256) double2 g_noalloc_partials[DST_NOALLOC_PARTIALS];
 
 static std::mutex g_noalloc_mutex;

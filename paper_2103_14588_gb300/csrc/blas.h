@@ -4,12 +4,12 @@
 #include "internal.h"
 
 #define DST_MAX_VEC 64            // basis vectors one projection / update handles
-#define DST_MAX_RED_BLOCKS 1216   // CTAs of a reduction pass (8 per SM)
+#define DST_MAX_RED_BLOCKS 456    // CTAs of a reduction pass (3 per SM)
 #define DST_MAX_DEVICES 64        // device ordinals the static-scratch entry point tracks
 
 int dst_reduction_blocks(int64_t n);
 int dst_k_project(int64_t n, int nvec, const double2 *V, const double2 *w, double2 *h, double2 *partials,
-                  int nblk, cudaStream_t s);
+                  int nblk, cudaStream_t s, double *wnrm2 = nullptr, double *wnrm_partials = nullptr);
 int dst_k_update(int64_t n, int nvec, const double2 *V, const double2 *h, double2 *w, double *nrm2,
                  double *partials, int nblk, cudaStream_t s);
 int dst_k_nrm2(int64_t n, const double2 *x, double *nrm2, double *partials, int nblk, cudaStream_t s);
@@ -19,3 +19,15 @@ int dst_k_scale(int64_t n, const double2 *src, double2 *dst, const double *nrm2,
 int dst_k_cast_64_32(int64_t n, const double2 *src, float2 *dst, cudaStream_t s);
 int dst_k_cast_32_64(int64_t n, const float2 *src, double2 *dst, cudaStream_t s);
 int dst_k_axpy1(int64_t n, const double2 *d, double2 *x, cudaStream_t s);
+int dst_k_reduce_partials(int nblk, int nvec, const double2 *partials, double2 *out, cudaStream_t s);
+int dst_k_reduce_real(int nblk, const double *partials, double *out, cudaStream_t s);
+
+// double-FP32 (df32) Arnoldi kernels (blas_df.cu); a df32 vector of n complex
+// entries is float2 hi[n] followed by float2 lo[n].
+int dst_k_project_df(int64_t n, int nvec, const float2 *V, const float2 *w, bool w_hi_only, double2 *h,
+                     double2 *partials, int nblk, cudaStream_t s, double *wnrm2, double *wnrm_partials);
+int dst_k_update_df(int64_t n, int nvec, const float2 *V, const double2 *h, float2 *w, bool w_hi_only, double *nrm2,
+                    double *partials, int nblk, cudaStream_t s);
+int dst_k_scale_df(int64_t n, float2 *v, const double *nrm2, cudaStream_t s);
+int dst_k_split_f64_df(int64_t n, const double2 *src, const double *nrm2, float2 *dst, cudaStream_t s);
+int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double2 *x, cudaStream_t s);

@@ -1,0 +1,365 @@
+// Arnoldi kernels in double-FP32 ("df32") arithmetic for the mixed-precision
+// solve.
+//
+// GB300 executes FP64 at 1/64 of its FP32 rate, so classical Gram-Schmidt in
+// native FP64 is bound by the FP64 pipe long before HBM.  These kernels keep
+// the Krylov basis of the FP32-apply GMRES cycles as pairs of FP32 planes,
+// value = hi + lo (|lo| <= ulp(hi)/2), which carry a 48-bit significand - the
+// same 16 bytes per complex entry as FP64 - and do the inner products and
+// updates with error-free transformations on the FP32 pipes:
+//   TwoProd(a, b): p = a*b, e = fma(a, b, -p)            (exact product, Dekker/FMA)
+//   TwoSum(a, b):  s = a+b, e = (a-(s-bb)) + (b-bb)       (exact sum, Knuth)
+// A df32 product (ah + al)(bh + bl) is p + (e + ah*bl + al*bh); sums run in a
+// (hi, lo) accumulator (the "double-single" arithmetic of Dekker 1971 and the
+// compensated dot product of Ogita, Rump & Oishi 2005).  Per-thread partial
+// sums are reduced across the warp in df32 (shuffles of hi and lo), converted
+// to FP64 once per warp and summed across warps and CTAs in FP64, in a fixed
+// order (deterministic).
+//
+// Layout of a df32 complex vector of n entries: float2 hi[n] followed by
+// float2 lo[n] (re, im interleaved in each plane).  The hi plane alone is the
+// vector rounded to FP32 - the input the FP32 operator apply reads directly.
+#include "blas.h"
+
+namespace dst {
+
+static constexpr int DF_THREADS = 256;
+static constexpr int DF_GROUP = 4;
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (p, e) with p + e = (ah + al)(bh + bl) up to the al*bl term (2^-48 relative)
+__device__ __forceinline__ void df_prod(float ah, float al, float bh, float bl, float &p, float &e) {
+    p = ah * bh;
+    e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+}
+
+struct DfAcc {
+    float hi, lo;
+    __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
+    // += p + e
+    __device__ __forceinline__ void add(float p, float e) {
+        float s, t;
+        two_sum(hi, p, s, t);
+        hi = s;
+        lo += t + e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// (ah, al) += (bh, bl) in df32, renormalised
+__device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e += al + bl;
+    ah = s + e;
+    al = e - (ah - s);
+}
+
+// Warp sum of a df32 value, in df32 (no FP64 work per lane); FP64 result
+// valid in lane 0.
+__device__ __forceinline__ double dfwarp_sum(DfAcc a) {
+    float h = a.hi, l = a.lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_down_sync(0xffffffffu, h, o);
+        const float bl = __shfl_down_sync(0xffffffffu, l, o);
+        df_add(h, l, bh, bl);
+    }
+    return (double)h + (double)l;
+}
+
+__device__ __forceinline__ double dwarp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Slices start at even entries so that two neighbouring complex entries of
+// a plane form one aligned 16-byte (float4) load; n is even for every mesh
+// (NC = 2 or 4 components per node).
+__device__ __forceinline__ void df_slice2(int64_t n, int64_t &b, int64_t &e) {
+    int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    per += per & 1;
+    b = (int64_t)blockIdx.x * per;
+    e = b + per < n ? b + per : n;
+}
+
+// acc += conj(v) w for one complex entry, df32 (v = vh + vl, w = ah + al)
+template <bool W_HI_ONLY>
+__device__ __forceinline__ void cdot_acc(float vhr, float vhi, float vlr, float vli, float ar, float ai, float alr,
+                                         float ali, DfAcc &re, DfAcc &im) {
+    float p1, e1, p2, e2;
+    df_prod(vhr, vlr, ar, W_HI_ONLY ? 0.f : alr, p1, e1);
+    df_prod(vhi, vli, ai, W_HI_ONLY ? 0.f : ali, p2, e2);
+    re.add(p1, e1);
+    re.add(p2, e2);
+    df_prod(vhr, vlr, ai, W_HI_ONLY ? 0.f : ali, p1, e1);
+    df_prod(vhi, vli, ar, W_HI_ONLY ? 0.f : alr, p2, e2);
+    im.add(p1, e1);
+    im.add(-p2, -e2);
+}
+
+// h_j partials = sum conj(V_j) w over the CTA's slice; ||w||^2 partials.
+// w_hi_only: w's lo plane is taken as zero (a fresh FP32 apply output).
+// Each thread takes two neighbouring entries per step (float4 loads of both
+// planes) and DF_GROUP basis vectors per sweep over its slice.
+template <bool W_HI_ONLY>
+__global__ void __launch_bounds__(DF_THREADS)
+project_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float2 *__restrict__ w,
+                  double2 *__restrict__ partials, double *__restrict__ wnrm_partials) {
+    constexpr int NW = DF_THREADS / 32;
+    __shared__ double red[NW][2 * DST_MAX_VEC + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t b, e;
+    df_slice2(n, b, e);
+    const float4 *wh = reinterpret_cast<const float4 *>(w), *wl = reinterpret_cast<const float4 *>(w + n);
+    DfAcc wn;
+    wn.zero();
+    for (int j0 = 0; j0 < nvec; j0 += DF_GROUP) {
+        const int gv = nvec - j0 < DF_GROUP ? nvec - j0 : DF_GROUP;
+        DfAcc re[DF_GROUP], im[DF_GROUP];
+#pragma unroll
+        for (int g = 0; g < DF_GROUP; ++g) { re[g].zero(); im[g].zero(); }
+        for (int64_t i = b + 2 * threadIdx.x; i < e; i += 2 * DF_THREADS) {
+            const int64_t q = i >> 1;
+            const float4 a = wh[q];
+            const float4 al = W_HI_ONLY ? make_float4(0.f, 0.f, 0.f, 0.f) : wl[q];
+            float4 vh[DF_GROUP], vl[DF_GROUP];
+#pragma unroll
+            for (int g = 0; g < DF_GROUP; ++g) {
+                if (g < gv) {
+                    const float4 *vj = reinterpret_cast<const float4 *>(V + (int64_t)(j0 + g) * 2 * n);
+                    vh[g] = vj[q];
+                    vl[g] = vj[(n >> 1) + q];
+                }
+            }
+            if (j0 == 0) {
+                float p, r;
+                df_prod(a.x, al.x, a.x, al.x, p, r); wn.add(p, r);
+                df_prod(a.y, al.y, a.y, al.y, p, r); wn.add(p, r);
+                df_prod(a.z, al.z, a.z, al.z, p, r); wn.add(p, r);
+                df_prod(a.w, al.w, a.w, al.w, p, r); wn.add(p, r);
+            }
+#pragma unroll
+            for (int g = 0; g < DF_GROUP; ++g) {
+                if (g < gv) {
+                    cdot_acc<W_HI_ONLY>(vh[g].x, vh[g].y, vl[g].x, vl[g].y, a.x, a.y, al.x, al.y, re[g], im[g]);
+                    cdot_acc<W_HI_ONLY>(vh[g].z, vh[g].w, vl[g].z, vl[g].w, a.z, a.w, al.z, al.w, re[g], im[g]);
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < DF_GROUP; ++g) {
+            if (g < gv) {
+                const double sr = dfwarp_sum(re[g]), si = dfwarp_sum(im[g]);
+                if (lane == 0) { red[warp][2 * (j0 + g)] = sr; red[warp][2 * (j0 + g) + 1] = si; }
+            }
+        }
+    }
+    const double wsum = dfwarp_sum(wn);
+    if (lane == 0) red[warp][2 * DST_MAX_VEC] = wsum;
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * nvec; q += DF_THREADS) {
+        double s_ = 0.0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) s_ += red[k][q];
+        reinterpret_cast<double *>(partials + (int64_t)blockIdx.x * nvec)[q] = s_;
+    }
+    if (wnrm_partials && threadIdx.x == 0) {
+        double s_ = 0.0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) s_ += red[k][2 * DST_MAX_VEC];
+        wnrm_partials[blockIdx.x] = s_;
+    }
+}
+
+// acc -= v c for one complex entry (v df32, c = (re_hi, re_lo, im_hi, im_lo))
+__device__ __forceinline__ void caxpy_sub(float vhr, float vhi, float vlr, float vli, const float4 &c, DfAcc &ar,
+                                          DfAcc &ai) {
+    float p1, e1, p2, e2;
+    df_prod(vhr, vlr, c.x, c.y, p1, e1);     // vr hr
+    df_prod(vhi, vli, c.z, c.w, p2, e2);     // vi hi
+    ar.add(-p1, -e1);
+    ar.add(p2, e2);
+    df_prod(vhr, vlr, c.z, c.w, p1, e1);     // vr hi
+    df_prod(vhi, vli, c.x, c.y, p2, e2);     // vi hr
+    ai.add(-p1, -e1);
+    ai.add(-p2, -e2);
+}
+
+__device__ __forceinline__ void renorm(DfAcc &a) {
+    const float s = a.hi + a.lo;
+    a.lo = a.lo - (s - a.hi);
+    a.hi = s;
+}
+
+// w <- w - sum_j V_j h_j in df32 (h given in FP64, split per CTA), and
+// partials of ||w||^2 after the update.  W_HI_ONLY: w's lo plane is read as
+// zero.  Two neighbouring entries per thread step, as in the projection.
+template <bool W_HI_ONLY>
+__global__ void __launch_bounds__(DF_THREADS)
+update_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double2 *__restrict__ h,
+                 float2 *__restrict__ w, double *__restrict__ nrm_partials) {
+    constexpr int NW = DF_THREADS / 32;
+    __shared__ float4 hs[DST_MAX_VEC];     // (re_hi, re_lo, im_hi, im_lo)
+    __shared__ double red[NW];
+    for (int j = threadIdx.x; j < nvec; j += DF_THREADS) {
+        const double2 c = h[j];
+        const float rh = (float)c.x, ih = (float)c.y;
+        hs[j] = make_float4(rh, (float)(c.x - (double)rh), ih, (float)(c.y - (double)ih));
+    }
+    __syncthreads();
+    int64_t b, e;
+    df_slice2(n, b, e);
+    float4 *wh = reinterpret_cast<float4 *>(w), *wl = reinterpret_cast<float4 *>(w + n);
+    DfAcc nr;
+    nr.zero();
+    for (int64_t i = b + 2 * threadIdx.x; i < e; i += 2 * DF_THREADS) {
+        const int64_t q = i >> 1;
+        const float4 a = wh[q];
+        const float4 al = W_HI_ONLY ? make_float4(0.f, 0.f, 0.f, 0.f) : wl[q];
+        DfAcc ar0, ai0, ar1, ai1;
+        ar0.hi = a.x; ar0.lo = al.x; ai0.hi = a.y; ai0.lo = al.y;
+        ar1.hi = a.z; ar1.lo = al.z; ai1.hi = a.w; ai1.lo = al.w;
+#pragma unroll 4
+        for (int j = 0; j < nvec; ++j) {
+            const float4 *vj = reinterpret_cast<const float4 *>(V + (int64_t)j * 2 * n);
+            const float4 vh = vj[q], vl = vj[(n >> 1) + q];
+            const float4 c = hs[j];
+            caxpy_sub(vh.x, vh.y, vl.x, vl.y, c, ar0, ai0);
+            caxpy_sub(vh.z, vh.w, vl.z, vl.w, c, ar1, ai1);
+        }
+        renorm(ar0); renorm(ai0); renorm(ar1); renorm(ai1);
+        wh[q] = make_float4(ar0.hi, ai0.hi, ar1.hi, ai1.hi);
+        wl[q] = make_float4(ar0.lo, ai0.lo, ar1.lo, ai1.lo);
+        float p, r;
+        df_prod(ar0.hi, ar0.lo, ar0.hi, ar0.lo, p, r); nr.add(p, r);
+        df_prod(ai0.hi, ai0.lo, ai0.hi, ai0.lo, p, r); nr.add(p, r);
+        df_prod(ar1.hi, ar1.lo, ar1.hi, ar1.lo, p, r); nr.add(p, r);
+        df_prod(ai1.hi, ai1.lo, ai1.hi, ai1.lo, p, r); nr.add(p, r);
+    }
+    const double s_ = dfwarp_sum(nr);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s_;
+    __syncthreads();
+    if (threadIdx.x == 0 && nrm_partials) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) t += red[k];
+        nrm_partials[blockIdx.x] = t;
+    }
+}
+
+// v <- v / sqrt(*nrm2) in df32 (both planes).
+__global__ void scale_df_kernel(int64_t n, float2 *__restrict__ v, const double *__restrict__ nrm2) {
+    const double sd = 1.0 / sqrt(*nrm2);
+    const float sh = (float)sd, sl = (float)(sd - (double)sh);
+    float2 *vh = v, *vl = v + n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 a = vh[i], al = vl[i];
+        float p, e, s, t;
+        df_prod(a.x, al.x, sh, sl, p, e);
+        s = p + e; t = e - (s - p);
+        float2 oh, ol;
+        oh.x = s; ol.x = t;
+        df_prod(a.y, al.y, sh, sl, p, e);
+        s = p + e; t = e - (s - p);
+        oh.y = s; ol.y = t;
+        vh[i] = oh;
+        vl[i] = ol;
+    }
+}
+
+// dst (df32) <- src (FP64) / sqrt(*nrm2): the restart vector of a cycle.
+__global__ void split_f64_df_kernel(int64_t n, const double2 *__restrict__ src, const double *__restrict__ nrm2,
+                                    float2 *__restrict__ dst) {
+    const double sc = 1.0 / sqrt(*nrm2);
+    float2 *dh = dst, *dl = dst + n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 a = src[i];
+        const double xr = a.x * sc, xi = a.y * sc;
+        const float hr = (float)xr, hi = (float)xi;
+        dh[i] = make_float2(hr, hi);
+        dl[i] = make_float2((float)(xr - (double)hr), (float)(xi - (double)hi));
+    }
+}
+
+// x (FP64) <- x + sum_j V_j y_j with V in df32 and y in FP64 (end of a cycle).
+__global__ void __launch_bounds__(DF_THREADS)
+combine_df_kernel(int64_t n, int k, const float2 *__restrict__ V, const double2 *__restrict__ y,
+                  double2 *__restrict__ x) {
+    __shared__ double2 ys[DST_MAX_VEC];
+    for (int j = threadIdx.x; j < k; j += DF_THREADS) ys[j] = y[j];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 acc = x[i];
+        for (int j = 0; j < k; ++j) {
+            const float2 *vj = V + (int64_t)j * 2 * n;
+            const float2 vh = vj[i], vl = vj[n + i];
+            const double vr = (double)vh.x + (double)vl.x, vi = (double)vh.y + (double)vl.y;
+            const double2 c = ys[j];
+            acc.x = fma(vr, c.x, fma(-vi, c.y, acc.x));
+            acc.y = fma(vr, c.y, fma(vi, c.x, acc.y));
+        }
+        x[i] = acc;
+    }
+}
+
+}  // namespace dst
+
+using namespace dst;
+
+static unsigned df_stream_blocks(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+int dst_k_project_df(int64_t n, int nvec, const float2 *V, const float2 *w, bool w_hi_only, double2 *h,
+                     double2 *partials, int nblk, cudaStream_t s, double *wnrm2, double *wnrm_partials) {
+    if (n & 1) return DST_ERR_ARG;     // two entries per 16-byte load
+    if (w_hi_only)
+        project_df_kernel<true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wnrm2 ? wnrm_partials : nullptr);
+    else
+        project_df_kernel<false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wnrm2 ? wnrm_partials : nullptr);
+    DST_CUDA_TRY(cudaGetLastError());
+    int rc = dst_k_reduce_partials(nblk, nvec, partials, h, s);
+    if (rc == DST_OK && wnrm2) rc = dst_k_reduce_real(nblk, wnrm_partials, wnrm2, s);
+    return rc;
+}
+
+int dst_k_update_df(int64_t n, int nvec, const float2 *V, const double2 *h, float2 *w, bool w_hi_only, double *nrm2,
+                    double *partials, int nblk, cudaStream_t s) {
+    if (n & 1) return DST_ERR_ARG;
+    if (w_hi_only)
+        update_df_kernel<true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, nrm2 ? partials : nullptr);
+    else
+        update_df_kernel<false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, nrm2 ? partials : nullptr);
+    DST_CUDA_TRY(cudaGetLastError());
+    if (nrm2) return dst_k_reduce_real(nblk, partials, nrm2, s);
+    return DST_OK;
+}
+
+int dst_k_scale_df(int64_t n, float2 *v, const double *nrm2, cudaStream_t s) {
+    scale_df_kernel<<<df_stream_blocks(n), 256, 0, s>>>(n, v, nrm2);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_split_f64_df(int64_t n, const double2 *src, const double *nrm2, float2 *dst, cudaStream_t s) {
+    split_f64_df_kernel<<<df_stream_blocks(n), 256, 0, s>>>(n, src, nrm2, dst);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double2 *x, cudaStream_t s) {
+    combine_df_kernel<<<df_stream_blocks(n), DF_THREADS, 0, s>>>(n, k, V, y, x);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}

@@ -2,18 +2,24 @@
 // (Algorithm 1 step 6: "solve the linear system by utilizing KSP"; the
 // Krylov method is GMRES, Saad & Schultz 1986, named in Sec. 2.2).
 //
-// Arnoldi uses classical Gram-Schmidt applied twice (CGS2): each pass is one
-// projection h = V^H w and one update w <- w - V h over the whole basis, so a
-// step reads the basis twice per pass instead of once per vector (MGS).  The
-// Hessenberg column goes to the host, which applies the Givens rotations and
-// tracks the least-squares residual |g_{j+1}|.  Every restart recomputes the
-// true residual b - A x in FP64.
+// Arnoldi uses classical Gram-Schmidt: one pass is a projection h = V^H w and
+// an update w <- w - V h over the whole basis (two streams over V instead of
+// one per basis vector as in modified Gram-Schmidt).  A second pass is made
+// when the DGKS test asks for it (Daniel, Gragg, Kaufman & Stewart 1976: the
+// norm after the pass fell below 1/sqrt(2) of the norm before), or always
+// (CGS2) on request.  The Hessenberg column goes to the host, which applies
+// the Givens rotations and tracks the least-squares residual |g_{j+1}|.  Every
+// restart recomputes the true residual b - A x in FP64.
 //
 // Mixed precision (iterative refinement): the outer loop keeps x, the
 // residual r = b - A x and the convergence test in FP64; each correction d
 // solves A d = r approximately with the same GMRES, whose operator apply
 // runs in FP32 (inputs rounded to FP32, output widened back to FP64), while
 // orthogonalisation, Givens rotations and the least-squares update stay FP64.
+// By default a correction is a single GMRES(m) cycle (or less, if it reaches
+// the inner tolerance), so the refinement is restarted GMRES whose restart
+// residual is recomputed with the FP64 operator.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -123,6 +129,59 @@ struct Prof {
     }
 };
 
+// Hessenberg matrix of one GMRES cycle reduced by complex Givens rotations
+// [[c, s], [-conj(s), c]] as columns arrive; g holds the rotated right-hand
+// side beta e_1, |g_{j+1}| the least-squares residual of the cycle.
+struct Hess {
+    int m;
+    std::vector<cplx> H, g, sn;
+    std::vector<double> cs;
+    explicit Hess(int m_) : m(m_), H((size_t)(m_ + 1) * m_), g(m_ + 1), sn(m_), cs(m_) {}
+    cplx &at(int i, int j) { return H[(size_t)i * m + j]; }
+    void start(double beta) {
+        std::fill(H.begin(), H.end(), cplx(0.0));
+        std::fill(g.begin(), g.end(), cplx(0.0));
+        g[0] = beta;
+    }
+    // column j: h[0..j] and h_{j+1,j} = hn; returns |g_{j+1}|
+    double add_column(int j, const cplx *h, double hn) {
+        for (int i = 0; i <= j; ++i) at(i, j) = h[i];
+        at(j + 1, j) = hn;
+        for (int i = 0; i < j; ++i) {
+            const cplx t = cs[i] * at(i, j) + sn[i] * at(i + 1, j);
+            at(i + 1, j) = -std::conj(sn[i]) * at(i, j) + cs[i] * at(i + 1, j);
+            at(i, j) = t;
+        }
+        const cplx a = at(j, j), b = at(j + 1, j);
+        if (std::abs(b) == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+        else if (std::abs(a) == 0.0) { cs[j] = 0.0; sn[j] = 1.0; }
+        else {
+            const double rho = std::sqrt(std::norm(a) + std::norm(b));
+            cs[j] = std::abs(a) / rho;
+            sn[j] = (a / std::abs(a)) * std::conj(b) / rho;
+        }
+        at(j, j) = cs[j] * a + sn[j] * b;
+        at(j + 1, j) = 0.0;
+        g[j + 1] = -std::conj(sn[j]) * g[j];
+        g[j] = cs[j] * g[j];
+        return std::abs(g[j + 1]);
+    }
+    // y = R(0:k,0:k)^{-1} g(0:k) by back substitution, written as sign * y
+    // (interleaved re, im) into out.
+    void solve(int k, double *out, double sign) {
+        std::vector<cplx> y(k);
+        for (int i = k - 1; i >= 0; --i) {
+            cplx acc = g[i];
+            for (int l = i + 1; l < k; ++l) acc -= at(i, l) * y[l];
+            y[i] = acc / at(i, i);
+        }
+        for (int i = 0; i < k; ++i) {
+            out[2 * i] = sign * y[i].real();
+            out[2 * i + 1] = sign * y[i].imag();
+        }
+    }
+};
+
 struct Solver {
     dst_mesh *mesh;
     cudaStream_t s;
@@ -131,6 +190,8 @@ struct Solver {
     double bytes = 0.0;
     int iters = 0;
     int restarts = 0;
+    int reorths = 0;
+    int ortho = 0;           // 0: DGKS selective second pass, 1: always two passes
     double resid_est = 0.0;
     Prof prof;
 
@@ -163,10 +224,10 @@ struct Solver {
         if (rc) return rc;
         return run(K_CAST, 1, 24.0 * n, 0.0, [&] { return dst_k_cast_32_64(w.n, w.y32, out, s); });
     }
-    int project(int nv, const double2 *wv, double2 *h) {
+    int project(int nv, const double2 *wv, double2 *h, double *wnrm2 = nullptr) {
         const double n = (double)w.n;
-        return run(K_PROJECT, 2, 16.0 * n * (nv + 1), 8.0 * n * nv,
-                   [&] { return dst_k_project(w.n, nv, w.V, wv, h, w.partials_c, nblk, s); });
+        return run(K_PROJECT, wnrm2 ? 3 : 2, 16.0 * n * (nv + 1), 8.0 * n * nv + (wnrm2 ? 4.0 * n : 0.0),
+                   [&] { return dst_k_project(w.n, nv, w.V, wv, h, w.partials_c, nblk, s, wnrm2, w.partials_r); });
     }
     int update(int nv, const double2 *h, double2 *x, double *nrm2) {
         const double n = (double)w.n;
@@ -217,95 +278,157 @@ struct Solver {
         return DST_OK;
     }
 
-    // Restarted GMRES(m) on A_prec x = rhs until ||rhs - A x|| <= tol_abs or
-    // max_iters Arnoldi steps in total (counted in this->iters).
+    // Hessenberg column j from the host buffer (first pass at host[0], second
+    // pass at host[2*MAXVEC], new norm^2 at host[4*MAXVEC]) into hs; returns
+    // DST_ERR_NAN on a non-finite column.
+    int take_column(Hess &hs, int j, bool &breakdown) {
+        const int nv = j + 1;
+        std::vector<cplx> col(nv);
+        for (int i = 0; i < nv; ++i)
+            col[i] = cplx(w.host[2 * i] + w.host[2 * DST_MAX_VEC + 2 * i],
+                          w.host[2 * i + 1] + w.host[2 * DST_MAX_VEC + 2 * i + 1]);
+        const double hn2 = w.host[4 * DST_MAX_VEC];
+        double colsq = 0.0;
+        for (auto &c : col) colsq += std::norm(c);
+        if (!std::isfinite(hn2) || !std::isfinite(colsq)) return DST_ERR_NAN;
+        resid_est = hs.add_column(j, col.data(), std::sqrt(hn2));
+        breakdown = std::sqrt(hn2) <= 1e-14 * std::sqrt(colsq + hn2);
+        return DST_OK;
+    }
+
+    // Restarted GMRES(m) on A_prec x = rhs, FP64 basis and FP64 Gram-Schmidt,
+    // until ||rhs - A x|| <= tol_abs, max_iters Arnoldi steps in total
+    // (this->iters) or max_cycles cycles; in the last case the caller computes
+    // the residual (beta_out = -1).
     int gmres(int prec, double2 *x, const double2 *rhs, bool x_zero, double tol_abs, int max_iters,
-              double &beta_out) {
+              double &beta_out, int max_cycles = 0x7fffffff) {
         const int m = w.m;
         const int64_t n = w.n;
         double beta;
         int rc = initial_residual(prec, x, rhs, x_zero, beta);
         if (rc) return rc;
         if (!std::isfinite(beta)) return DST_ERR_NAN;
-        std::vector<cplx> H((size_t)(m + 1) * m), g(m + 1), sn(m), y(m);
-        std::vector<double> cs(m);
-        auto Hat = [&](int i, int j) -> cplx & { return H[(size_t)i * m + j]; };
+        Hess hs(m);
         bool breakdown = false;
+        int cycles = 0;
         while (beta > tol_abs && iters < max_iters && !breakdown) {
             if ((rc = scale(w.V))) return rc;   // V0 = r / beta
-            std::fill(g.begin(), g.end(), cplx(0.0));
-            std::fill(H.begin(), H.end(), cplx(0.0));
-            g[0] = beta;
+            hs.start(beta);
             int k = 0;
             for (int j = 0; j < m; ++j) {
                 double2 *vj = w.V + (size_t)j * n;
                 double2 *wv = w.V + (size_t)(j + 1) * n;
                 if ((rc = apply(prec, vj, wv))) return rc;
                 const int nv = j + 1;
-                // CGS2: two projection + update passes
-                if ((rc = project(nv, wv, w.h1))) return rc;
-                if ((rc = update(nv, w.h1, wv, nullptr))) return rc;
-                if ((rc = project(nv, wv, w.h2))) return rc;
-                if ((rc = update(nv, w.h2, wv, w.nrm))) return rc;
-                // normalise on the device straight away (1/sqrt(nrm)), then read the column
-                if ((rc = scale(wv))) return rc;
+                // classical Gram-Schmidt pass; ||A v_j||^2 (before) into nrm[3], ||w||^2 (after) into nrm[0]
+                if ((rc = project(nv, wv, w.h1, w.nrm + 3))) return rc;
+                if ((rc = update(nv, w.h1, wv, w.nrm))) return rc;
                 DST_CUDA_TRY(cudaMemcpyAsync(w.host, w.h1, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
-                DST_CUDA_TRY(cudaMemcpyAsync(w.host + 2 * DST_MAX_VEC, w.h2, sizeof(double2) * nv,
-                                             cudaMemcpyDeviceToHost, s));
-                DST_CUDA_TRY(cudaMemcpyAsync(w.host + 4 * DST_MAX_VEC, w.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+                DST_CUDA_TRY(cudaMemcpyAsync(w.host + 4 * DST_MAX_VEC, w.nrm, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+                bool second = ortho == 1;
+                if (!second) {
+                    if ((rc = sync())) return rc;
+                    second = w.host[4 * DST_MAX_VEC] < 0.5 * w.host[4 * DST_MAX_VEC + 3];   // DGKS
+                }
+                if (second) {
+                    ++reorths;
+                    if ((rc = project(nv, wv, w.h2))) return rc;
+                    if ((rc = update(nv, w.h2, wv, w.nrm))) return rc;
+                    DST_CUDA_TRY(cudaMemcpyAsync(w.host + 2 * DST_MAX_VEC, w.h2, sizeof(double2) * nv,
+                                                 cudaMemcpyDeviceToHost, s));
+                    DST_CUDA_TRY(cudaMemcpyAsync(w.host + 4 * DST_MAX_VEC, w.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+                } else {
+                    for (int i = 0; i < 2 * nv; ++i) w.host[2 * DST_MAX_VEC + i] = 0.0;
+                }
+                // normalise on the device (1/sqrt(nrm)), then read the column
+                if ((rc = scale(wv))) return rc;
                 if ((rc = sync())) return rc;
                 ++iters;
-                double colsq = 0.0;
-                for (int i = 0; i < nv; ++i) {
-                    cplx hv(w.host[2 * i] + w.host[2 * DST_MAX_VEC + 2 * i],
-                            w.host[2 * i + 1] + w.host[2 * DST_MAX_VEC + 2 * i + 1]);
-                    Hat(i, j) = hv;
-                    colsq += std::norm(hv);
-                }
-                const double hn2 = w.host[4 * DST_MAX_VEC];
-                if (!std::isfinite(hn2) || !std::isfinite(colsq)) return DST_ERR_NAN;
-                const double hn = std::sqrt(hn2);
-                Hat(j + 1, j) = hn;
-                for (int i = 0; i < j; ++i) {           // previous rotations
-                    cplx t = cs[i] * Hat(i, j) + sn[i] * Hat(i + 1, j);
-                    Hat(i + 1, j) = -std::conj(sn[i]) * Hat(i, j) + cs[i] * Hat(i + 1, j);
-                    Hat(i, j) = t;
-                }
-                // new rotation zeroing H(j+1, j)
-                const cplx a = Hat(j, j), bb = Hat(j + 1, j);
-                if (std::abs(bb) == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
-                else if (std::abs(a) == 0.0) { cs[j] = 0.0; sn[j] = 1.0; }
-                else {
-                    const double rho = std::sqrt(std::norm(a) + std::norm(bb));
-                    cs[j] = std::abs(a) / rho;
-                    sn[j] = (a / std::abs(a)) * std::conj(bb) / rho;
-                }
-                Hat(j, j) = cs[j] * a + sn[j] * bb;
-                Hat(j + 1, j) = 0.0;
-                g[j + 1] = -std::conj(sn[j]) * g[j];
-                g[j] = cs[j] * g[j];
+                if ((rc = take_column(hs, j, breakdown))) return rc;
                 k = j + 1;
-                resid_est = std::abs(g[j + 1]);
-                if (hn <= 1e-14 * std::sqrt(colsq + hn2)) { breakdown = true; break; }
-                if (resid_est <= tol_abs || iters >= max_iters) break;
+                if (breakdown || resid_est <= tol_abs || iters >= max_iters) break;
             }
-            // y = H(0:k,0:k)^{-1} g(0:k), back substitution; x += V y (update with h = -y)
-            for (int i = k - 1; i >= 0; --i) {
-                cplx acc = g[i];
-                for (int l = i + 1; l < k; ++l) acc -= Hat(i, l) * y[l];
-                y[i] = acc / Hat(i, i);
-            }
-            for (int i = 0; i < k; ++i) {
-                w.host[2 * i] = -y[i].real();
-                w.host[2 * i + 1] = -y[i].imag();
-            }
+            // x += V y  (update with h = -y)
+            hs.solve(k, w.host, -1.0);
             DST_CUDA_TRY(cudaMemcpyAsync(w.h1, w.host, sizeof(double2) * k, cudaMemcpyHostToDevice, s));
             if ((rc = update(k, w.h1, x, nullptr))) return rc;
             ++restarts;
+            if (++cycles >= max_cycles) {
+                beta_out = -1.0;
+                return DST_OK;
+            }
             if ((rc = initial_residual(prec, x, rhs, false, beta))) return rc;
             if (!std::isfinite(beta)) return DST_ERR_NAN;
         }
         beta_out = beta;
+        return DST_OK;
+    }
+
+    // One GMRES(m) cycle for the correction equation A d = r (d = 0 on entry),
+    // FP32 operator apply on a df32 basis with df32 Gram-Schmidt: V_0 = r/||r||
+    // (||r||^2 in w.nrm[rslot]), d += V y at the end (FP64).
+    int cycle_df(double2 *d, const double2 *r, int rslot, double rnorm, double tol_abs, int max_iters) {
+        const int m = w.m;
+        const int64_t n = w.n;
+        const double dn = (double)n;
+        float2 *Vd = reinterpret_cast<float2 *>(w.V);   // (m+1) df32 vectors, 2n float2 each
+        int rc = run(K_SCALE, 1, 32.0 * dn, 2.0 * dn,
+                     [&] { return dst_k_split_f64_df(n, r, w.nrm + rslot, Vd, s); });
+        if (rc) return rc;
+        Hess hs(m);
+        hs.start(rnorm);
+        bool breakdown = false;
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            float2 *vj = Vd + (size_t)j * 2 * n;
+            float2 *wv = Vd + (size_t)(j + 1) * 2 * n;
+            const int nv = j + 1;
+            // FP32 apply straight from the hi plane of v_j into the hi plane of w
+            if ((rc = run(K_APPLY32, 1, 16.0 * dn, 0.0,
+                          [&] { return dst_internal_apply(mesh, DST_FP32, vj, wv, s); })))
+                return rc;
+            if ((rc = run(K_PROJECT, 3, 16.0 * dn * nv + 8.0 * dn, 8.0 * dn * nv,
+                          [&] { return dst_k_project_df(n, nv, Vd, wv, true, w.h1, w.partials_c, nblk, s, w.nrm + 3,
+                                                        w.partials_r); })))
+                return rc;
+            if ((rc = run(K_UPDATE, 2, 16.0 * dn * nv + 24.0 * dn, 8.0 * dn * nv,
+                          [&] { return dst_k_update_df(n, nv, Vd, w.h1, wv, true, w.nrm, w.partials_r, nblk, s); })))
+                return rc;
+            DST_CUDA_TRY(cudaMemcpyAsync(w.host, w.h1, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
+            DST_CUDA_TRY(cudaMemcpyAsync(w.host + 4 * DST_MAX_VEC, w.nrm, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            bool second = ortho == 1;
+            if (!second) {
+                if ((rc = sync())) return rc;
+                second = w.host[4 * DST_MAX_VEC] < 0.5 * w.host[4 * DST_MAX_VEC + 3];   // DGKS
+            }
+            if (second) {
+                ++reorths;
+                if ((rc = run(K_PROJECT, 2, 16.0 * dn * (nv + 1), 8.0 * dn * nv,
+                              [&] { return dst_k_project_df(n, nv, Vd, wv, false, w.h2, w.partials_c, nblk, s, nullptr,
+                                                            nullptr); })))
+                    return rc;
+                if ((rc = run(K_UPDATE, 2, 16.0 * dn * (nv + 2), 8.0 * dn * nv,
+                              [&] { return dst_k_update_df(n, nv, Vd, w.h2, wv, false, w.nrm, w.partials_r, nblk, s); })))
+                    return rc;
+                DST_CUDA_TRY(cudaMemcpyAsync(w.host + 2 * DST_MAX_VEC, w.h2, sizeof(double2) * nv,
+                                             cudaMemcpyDeviceToHost, s));
+                DST_CUDA_TRY(cudaMemcpyAsync(w.host + 4 * DST_MAX_VEC, w.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+            } else {
+                for (int i = 0; i < 2 * nv; ++i) w.host[2 * DST_MAX_VEC + i] = 0.0;
+            }
+            if ((rc = run(K_SCALE, 1, 32.0 * dn, 6.0 * dn, [&] { return dst_k_scale_df(n, wv, w.nrm, s); }))) return rc;
+            if ((rc = sync())) return rc;
+            ++iters;
+            if ((rc = take_column(hs, j, breakdown))) return rc;
+            k = j + 1;
+            if (breakdown || resid_est <= tol_abs || iters >= max_iters) break;
+        }
+        hs.solve(k, w.host, 1.0);
+        DST_CUDA_TRY(cudaMemcpyAsync(w.h1, w.host, sizeof(double2) * k, cudaMemcpyHostToDevice, s));
+        if ((rc = run(K_UPDATE, 1, 16.0 * dn * k + 32.0 * dn, 8.0 * dn * k,
+                      [&] { return dst_k_combine_df(n, k, Vd, w.h1, d, s); })))
+            return rc;
+        ++restarts;
         return DST_OK;
     }
 };
@@ -319,9 +442,12 @@ extern "C" int dst_default_solve_opts(dst_solve_opts *o) {
     o->rtol = 1e-8;
     o->mixed_precision = 0;
     o->inner_rtol = 1e-4;
-    o->max_refine = 50;
+    o->max_refine = 100000;
+    o->inner_cycles = 1;
     o->use_initial_guess = 0;
     o->profile = 0;
+    o->ortho = 0;
+    o->mixed_ortho = 0;
     return DST_OK;
 }
 
@@ -332,6 +458,7 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     sv.mesh = mesh;
     sv.s = s;
     sv.nblk = dst_reduction_blocks(mesh->n_unknowns);
+    sv.ortho = o.ortho;
     int rc = setup_workspace(mesh, o.restart, mixed, sv.w);
     if (rc) return rc;
     static thread_local double *pinned = nullptr;
@@ -377,12 +504,23 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
             if ((rc = sv.sync())) return rc;
             rnorm = std::sqrt(sv.w.host[0]);
         }
+        // df32 Gram-Schmidt needs the correction to be one cycle from d = 0;
+        // the r64 residual norm^2 must sit in nrm[2] for the first split
+        const bool use_df = o.mixed_ortho == 0 && o.inner_cycles == 1;
+        if (!o.use_initial_guess) {
+            DST_CUDA_TRY(cudaMemcpyAsync(sv.w.nrm + 2, sv.w.nrm + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
         int refine = 0;
         while (rnorm > tol && refine < o.max_refine && sv.iters < o.max_iters) {
             if (!std::isfinite(rnorm)) return DST_ERR_NAN;
             double inner_beta;
             DST_CUDA_TRY(cudaMemsetAsync(sv.w.d, 0, sizeof(double2) * n, s));
-            rc = sv.gmres(DST_FP32, sv.w.d, sv.w.r64, true, o.inner_rtol * rnorm, o.max_iters, inner_beta);
+            const double itol = std::max(o.inner_rtol * rnorm, 0.5 * tol);
+            if (use_df)
+                rc = sv.cycle_df(sv.w.d, sv.w.r64, 2, rnorm, itol, o.max_iters);
+            else
+                rc = sv.gmres(DST_FP32, sv.w.d, sv.w.r64, true, itol, o.max_iters, inner_beta,
+                              o.inner_cycles > 0 ? o.inner_cycles : 0x7fffffff);
             if (rc) return rc;
             if ((rc = sv.run(K_MISC, 1, 48.0 * n, 2.0 * n, [&] { return dst_k_axpy1(n, sv.w.d, psi, s); }))) return rc;
             if ((rc = sv.apply(DST_FP64, psi, sv.w.tmp))) return rc;
@@ -404,6 +542,7 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
         st.launches += sv.prof.launches[c];
     }
     st.iters = sv.iters;
+    st.reorths = sv.reorths;
     st.restarts = sv.restarts;
     st.rel_resid_true = beta / bnorm;
     st.rel_resid_est = sv.resid_est / bnorm;
@@ -421,7 +560,8 @@ extern "C" int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, 
     dst_default_solve_opts(&o);
     if (opts) o = *opts;
     if (!mesh || !psi || o.restart < 1 || o.restart > DST_MAX_VEC - 1 || o.max_iters < 0 || !(o.rtol >= 0) ||
-        (o.mixed_precision && (!(o.inner_rtol > 0) || o.max_refine < 1))) {
+        (o.mixed_precision && (!(o.inner_rtol > 0) || o.max_refine < 1)) || o.ortho < 0 || o.ortho > 1 ||
+        o.mixed_ortho < 0 || o.mixed_ortho > 1 || o.inner_cycles < 0) {
         rc = DST_ERR_ARG;
     } else if (!mesh->d_psi0) {
         rc = DST_ERR_STATE;

@@ -35,7 +35,7 @@ struct OpParams {
     int64_t nt;              // unknown time layers N_t
     double ht;               // time element size
     double m;                // mass
-    int vmode;               // 0: separable (x-only weights), 1: general per-element V
+    int vmode;               // 0: x-only weights, 1: general per-element V, 2: no potential
     const double *wx;        // separable: [2*nel_x]: (m + V_ex) then (-m + V_ex)
     const double *Vel;       // general: V per spatial element (x fastest)
 };

@@ -45,7 +45,7 @@ OpParams dst_internal_params(const dst_mesh *mesh) {
     p.nt = mesh->nt;
     p.ht = mesh->ht;
     p.m = mesh->m;
-    p.vmode = mesh->v_general ? 1 : 0;
+    p.vmode = mesh->v_general ? 1 : (mesh->V.empty() ? 2 : 0);
     p.wx = mesh->d_wx;
     p.Vel = mesh->d_V;
     return p;
@@ -230,6 +230,10 @@ int dst_internal_rhs(const dst_mesh *mesh, double2 *b, cudaStream_t s) {
 extern "C" int dst_apply_operator(const dst_mesh *mesh, int precision, const void *x, void *y, void *stream) {
     if (!mesh || !x || !y || (precision != DST_FP64 && precision != DST_FP32)) return DST_ERR_ARG;
     if (x == y) return DST_ERR_ARG;
+    if (((uintptr_t)x | (uintptr_t)y) & 15) {
+        dst_internal_set_error_detail("dst_apply_operator: x and y must be 16-byte aligned");
+        return DST_ERR_ARG;
+    }
     return dst_internal_apply(mesh, precision, x, y, (cudaStream_t)stream);
 }
 

@@ -110,16 +110,48 @@ def test_plane_wave_config_solution(torch, B):
     assert 5.0e-5 < rel_l2(x, ex) < 6.5e-5
 
 
+@pytest.mark.parametrize("mixed_ortho", [0, 1])
 @pytest.mark.parametrize("d,n_el,bc", [(1, [64, 1, 1, 64], [P]), (2, [12, 10, 1, 14], [P, P]),
                                        (3, [5, 4, 4, 5], [P, D, D])])
-def test_mixed_precision_refinement(torch, B, d, n_el, bc):
+def test_mixed_precision_refinement(torch, B, d, n_el, bc, mixed_ortho):
+    """FP32 apply + FP64 refinement, inner Gram-Schmidt in double-FP32 (0) or FP64 (1)."""
     w = W.plane_wave_1p1(n=64) if d == 1 else W.random_mesh(d, n_el, bc, seed=80 + d)
     ref, _, _ = _exact(w)
     x, st = _solve(torch, B, w, restart=30, rtol=1e-12, max_iters=50000, mixed_precision=1,
-                   inner_rtol=1e-4, max_refine=40)
+                   mixed_ortho=mixed_ortho)
     assert st["status"] == 0 and st["refinements"] >= 2
     assert st["rel_resid_true"] <= 1e-12
     assert rel_l2(x, ref) <= 1e-8
+
+
+@pytest.mark.parametrize("ortho", [0, 1])
+def test_mixed_until_inner_tolerance_and_cgs2(torch, B, ortho):
+    """Refinement steps that run GMRES to the inner tolerance (several cycles),
+    and always-two-pass Gram-Schmidt, reach the same solution."""
+    w = W.random_mesh(2, [12, 10, 1, 14], [P, P], seed=81)
+    ref, _, _ = _exact(w)
+    x, st = _solve(torch, B, w, restart=30, rtol=1e-12, max_iters=50000, mixed_precision=1,
+                   inner_cycles=0, inner_rtol=1e-4, max_refine=40, ortho=ortho)
+    assert st["status"] == 0 and 2 <= st["refinements"] <= 6
+    assert rel_l2(x, ref) <= 1e-8
+    if ortho == 1:
+        assert st["reorths"] == st["iters"]
+
+
+def test_full_size_fp64_solve_matches_oracle_step_count(torch, B):
+    """The FP64 GMRES(30) solve of the 96^2 x 96 Zitterbewegung system takes the
+    number of Arnoldi steps the oracle's own GMRES took (recorded by
+    oracle/iteration_counts.py) and stops at the same residual."""
+    import json
+    import os
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_iteration_counts.json")))
+    w = W.zb_2p1()
+    x, st = _solve(torch, B, w, restart=30, rtol=1e-8, max_iters=20000)
+    assert st["status"] == 0
+    assert abs(st["iters"] - rec["zb_2p1"]["iters"]) <= 2
+    assert st["rel_resid_true"] <= 1e-8
+    if st["iters"] == rec["zb_2p1"]["iters"]:
+        assert abs(st["rel_resid_true"] - rec["zb_2p1"]["rel_resid_true"]) <= 1e-3 * rec["zb_2p1"]["rel_resid_true"]
 
 
 def test_warm_start_from_solution(torch, B):
