@@ -34,6 +34,13 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;
 }
 
+// Second Gram-Schmidt pass gate evaluated on the device: nrm[0] = ||w||^2
+// after the first pass, nrm[3] = ||A v_j||^2 before it (DGKS: reorthogonalise
+// when ||w|| < ||A v_j|| / sqrt 2).  A null gate means "always run".
+__device__ __forceinline__ bool dgks_skip(const double *gate) {
+    return gate != nullptr && !(gate[0] < 0.5 * gate[3]);
+}
+
 __device__ __forceinline__ void slice(int64_t n, int64_t &b, int64_t &e) {
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     b = (int64_t)blockIdx.x * per;
@@ -47,7 +54,8 @@ __device__ __forceinline__ void slice(int64_t n, int64_t &b, int64_t &e) {
 // warps' values are summed in warp order.
 __global__ void __launch_bounds__(RED_THREADS)
 project_partial_kernel(int64_t n, int nvec, const double2 *__restrict__ V, const double2 *__restrict__ w,
-                       double2 *__restrict__ partials, double *__restrict__ wnrm_partials) {
+                       double2 *__restrict__ partials, double *__restrict__ wnrm_partials, const double *gate) {
+    if (dgks_skip(gate)) return;
     constexpr int NW = RED_THREADS / 32;
     __shared__ double red[NW][2 * DST_MAX_VEC + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -98,9 +106,14 @@ project_partial_kernel(int64_t n, int nvec, const double2 *__restrict__ V, const
 
 // out[j] = sum_blk partials[blk * nvec + j]   (one CTA per j)
 __global__ void __launch_bounds__(RED_THREADS)
-reduce_partials_kernel(int nblk, int nvec, const double2 *__restrict__ partials, double2 *__restrict__ out) {
+reduce_partials_kernel(int nblk, int nvec, const double2 *__restrict__ partials, double2 *__restrict__ out,
+                       const double *gate) {
     __shared__ double sh[RED_THREADS / 32];
     const int j = blockIdx.x;
+    if (dgks_skip(gate)) {
+        if (threadIdx.x == 0) out[j] = make_double2(0.0, 0.0);
+        return;
+    }
     double sr = 0.0, si = 0.0;
     for (int k = threadIdx.x; k < nblk; k += RED_THREADS) {
         const double2 v = partials[(int64_t)k * nvec + j];
@@ -115,7 +128,8 @@ reduce_partials_kernel(int nblk, int nvec, const double2 *__restrict__ partials,
 // w <- w - sum_j V_j h_j ; partial ||w||^2 per CTA.
 __global__ void __launch_bounds__(RED_THREADS)
 update_kernel(int64_t n, int nvec, const double2 *__restrict__ V, const double2 *__restrict__ h,
-              double2 *__restrict__ w, double *__restrict__ nrm_partials) {
+              double2 *__restrict__ w, double *__restrict__ nrm_partials, const double *gate) {
+    if (dgks_skip(gate)) return;
     __shared__ double2 hs[DST_MAX_VEC];
     __shared__ double sh[RED_THREADS / 32];
     for (int j = threadIdx.x; j < nvec; j += RED_THREADS) hs[j] = h[j];
@@ -139,12 +153,17 @@ update_kernel(int64_t n, int nvec, const double2 *__restrict__ V, const double2 
 }
 
 __global__ void __launch_bounds__(RED_THREADS)
-reduce_real_kernel(int nblk, const double *__restrict__ partials, double *__restrict__ out) {
+reduce_real_kernel(int nblk, const double *__restrict__ partials, double *out, const double *gate,
+                   double *counter) {
+    if (dgks_skip(gate)) return;
     __shared__ double sh[RED_THREADS / 32];
     double s = 0.0;
     for (int k = threadIdx.x; k < nblk; k += RED_THREADS) s += partials[k];
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) *out = s;
+    if (threadIdx.x == 0) {
+        *out = s;
+        if (counter) *counter += 1.0;
+    }
 }
 
 // ||x||^2 partials
@@ -183,7 +202,10 @@ residual_kernel(int64_t n, const double2 *__restrict__ b_, const double2 *__rest
 // dst = src * (1/sqrt(*nrm2)) (or * scale when nrm2 is null)
 __global__ void scale_kernel(int64_t n, const double2 *__restrict__ src, double2 *__restrict__ dst,
                              const double *__restrict__ nrm2, double scale) {
-    const double s = nrm2 ? 1.0 / sqrt(*nrm2) : scale;
+    __shared__ double s_sh;       // 1/sqrt once per CTA: FP64 division is slow here
+    if (threadIdx.x == 0) s_sh = nrm2 ? 1.0 / sqrt(*nrm2) : scale;
+    __syncthreads();
+    const double s = s_sh;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double2 v = src[i];
         dst[i] = make_double2(v.x * s, v.y * s);
@@ -223,37 +245,40 @@ static unsigned stream_blocks(int64_t n) {
 }
 
 int dst_k_project(int64_t n, int nvec, const double2 *V, const double2 *w, double2 *h, double2 *partials,
-                  int nblk, cudaStream_t s, double *wnrm2, double *wnrm_partials) {
-    project_partial_kernel<<<nblk, RED_THREADS, 0, s>>>(n, nvec, V, w, partials, wnrm2 ? wnrm_partials : nullptr);
-    reduce_partials_kernel<<<nvec, RED_THREADS, 0, s>>>(nblk, nvec, partials, h);
-    if (wnrm2) reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, wnrm_partials, wnrm2);
+                  int nblk, cudaStream_t s, double *wnrm2, double *wnrm_partials, const double *gate) {
+    project_partial_kernel<<<nblk, RED_THREADS, 0, s>>>(n, nvec, V, w, partials, wnrm2 ? wnrm_partials : nullptr,
+                                                        gate);
+    reduce_partials_kernel<<<nvec, RED_THREADS, 0, s>>>(nblk, nvec, partials, h, gate);
+    if (wnrm2) reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, wnrm_partials, wnrm2, gate, nullptr);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
 
-int dst_k_reduce_partials(int nblk, int nvec, const double2 *partials, double2 *out, cudaStream_t s) {
-    reduce_partials_kernel<<<nvec, RED_THREADS, 0, s>>>(nblk, nvec, partials, out);
+int dst_k_reduce_partials(int nblk, int nvec, const double2 *partials, double2 *out, cudaStream_t s,
+                          const double *gate) {
+    reduce_partials_kernel<<<nvec, RED_THREADS, 0, s>>>(nblk, nvec, partials, out, gate);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
 
-int dst_k_reduce_real(int nblk, const double *partials, double *out, cudaStream_t s) {
-    reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, out);
+int dst_k_reduce_real(int nblk, const double *partials, double *out, cudaStream_t s, const double *gate,
+                      double *counter) {
+    reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, out, gate, counter);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
 
 int dst_k_update(int64_t n, int nvec, const double2 *V, const double2 *h, double2 *w, double *nrm2,
-                 double *partials, int nblk, cudaStream_t s) {
-    update_kernel<<<nblk, RED_THREADS, 0, s>>>(n, nvec, V, h, w, nrm2 ? partials : nullptr);
-    if (nrm2) reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, nrm2);
+                 double *partials, int nblk, cudaStream_t s, const double *gate, double *counter) {
+    update_kernel<<<nblk, RED_THREADS, 0, s>>>(n, nvec, V, h, w, nrm2 ? partials : nullptr, gate);
+    if (nrm2) reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, nrm2, gate, counter);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
 
 int dst_k_nrm2(int64_t n, const double2 *x, double *nrm2, double *partials, int nblk, cudaStream_t s) {
     nrm2_partial_kernel<<<nblk, RED_THREADS, 0, s>>>(n, x, partials);
-    reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, nrm2);
+    reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, nrm2, nullptr, nullptr);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
@@ -261,7 +286,7 @@ int dst_k_nrm2(int64_t n, const double2 *x, double *nrm2, double *partials, int 
 int dst_k_residual(int64_t n, const double2 *b, const double2 *y, double2 *r, double *nrm2, double *partials,
                    int nblk, cudaStream_t s) {
     residual_kernel<<<nblk, RED_THREADS, 0, s>>>(n, b, y, r, partials);
-    reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, nrm2);
+    reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, nrm2, nullptr, nullptr);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
@@ -290,8 +315,14 @@ int dst_k_axpy1(int64_t n, const double2 *d, double2 *x, cudaStream_t s) {
     return DST_OK;
 }
 
-int dst_reduction_blocks(int64_t n) {
+int dst_projection_blocks(int64_t n) {
     int64_t b = (n + 4095) / 4096;
+    if (b > 456) b = 456;
+    return (int)(b < 1 ? 1 : b);
+}
+
+int dst_reduction_blocks(int64_t n) {
+    int64_t b = (n + 2047) / 2048;
     if (b > DST_MAX_RED_BLOCKS) b = DST_MAX_RED_BLOCKS;
     return (int)(b < 1 ? 1 : b);
 }

@@ -110,10 +110,18 @@ __device__ __forceinline__ void cdot_acc(float vhr, float vhi, float vlr, float 
 // w_hi_only: w's lo plane is taken as zero (a fresh FP32 apply output).
 // Each thread takes two neighbouring entries per step (float4 loads of both
 // planes) and DF_GROUP basis vectors per sweep over its slice.
+// The last CTA to finish (atomic ticket) sums every CTA's partials in CTA
+// order and writes h (and ||w||^2): a deterministic single-kernel reduction.
 template <bool W_HI_ONLY>
 __global__ void __launch_bounds__(DF_THREADS)
 project_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float2 *__restrict__ w,
-                  double2 *__restrict__ partials, double *__restrict__ wnrm_partials) {
+                  double2 *__restrict__ partials, double *__restrict__ wnrm_partials, const double *gate,
+                  double2 *__restrict__ h, double *__restrict__ wnrm2, unsigned *__restrict__ ticket) {
+    if (gate != nullptr && !(gate[0] < 0.5 * gate[3])) {           // DGKS: no second pass needed
+        if (blockIdx.x == 0)
+            for (int j = threadIdx.x; j < nvec; j += DF_THREADS) h[j] = make_double2(0.0, 0.0);
+        return;
+    }
     constexpr int NW = DF_THREADS / 32;
     __shared__ double red[NW][2 * DST_MAX_VEC + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -178,6 +186,31 @@ project_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float
         for (int k = 0; k < NW; ++k) s_ += red[k][2 * DST_MAX_VEC];
         wnrm_partials[blockIdx.x] = s_;
     }
+    // last CTA: final reduction over CTAs in CTA order
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // one warp per value: lanes stride over the CTAs, then a fixed shuffle tree
+    const double *pd = reinterpret_cast<const double *>(partials);
+    for (int q = warp; q < 2 * nvec + 1; q += NW) {
+        double s_ = 0.0;
+        if (q < 2 * nvec) {
+            for (unsigned k = lane; k < gridDim.x; k += 32) s_ += __ldcg(pd + (size_t)k * 2 * nvec + q);
+        } else if (wnrm2) {
+            for (unsigned k = lane; k < gridDim.x; k += 32) s_ += __ldcg(wnrm_partials + k);
+        }
+        s_ = dwarp_sum(s_);
+        if (lane == 0) {
+            if (q < 2 * nvec) reinterpret_cast<double *>(h)[q] = s_;
+            else if (wnrm2) *wnrm2 = s_;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // acc -= v c for one complex entry (v df32, c = (re_hi, re_lo, im_hi, im_lo))
@@ -206,7 +239,9 @@ __device__ __forceinline__ void renorm(DfAcc &a) {
 template <bool W_HI_ONLY>
 __global__ void __launch_bounds__(DF_THREADS)
 update_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double2 *__restrict__ h,
-                 float2 *__restrict__ w, double *__restrict__ nrm_partials) {
+                 float2 *__restrict__ w, double *__restrict__ nrm_partials, const double *gate,
+                 double *__restrict__ nrm2, double *__restrict__ counter, unsigned *__restrict__ ticket) {
+    if (gate != nullptr && !(gate[0] < 0.5 * gate[3])) return;     // DGKS: no second pass needed
     constexpr int NW = DF_THREADS / 32;
     __shared__ float4 hs[DST_MAX_VEC];     // (re_hi, re_lo, im_hi, im_lo)
     __shared__ double red[NW];
@@ -228,13 +263,21 @@ update_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double
         DfAcc ar0, ai0, ar1, ai1;
         ar0.hi = a.x; ar0.lo = al.x; ai0.hi = a.y; ai0.lo = al.y;
         ar1.hi = a.z; ar1.lo = al.z; ai1.hi = a.w; ai1.lo = al.w;
-#pragma unroll 4
+        // software pipelining: the planes of V_{j+1} are loaded before V_j is combined
+        const float4 *v0 = reinterpret_cast<const float4 *>(V);
+        float4 vh = v0[q], vl = v0[(n >> 1) + q];
         for (int j = 0; j < nvec; ++j) {
-            const float4 *vj = reinterpret_cast<const float4 *>(V + (int64_t)j * 2 * n);
-            const float4 vh = vj[q], vl = vj[(n >> 1) + q];
+            float4 nh = vh, nl = vl;
+            if (j + 1 < nvec) {
+                const float4 *vn = reinterpret_cast<const float4 *>(V + (int64_t)(j + 1) * 2 * n);
+                nh = vn[q];
+                nl = vn[(n >> 1) + q];
+            }
             const float4 c = hs[j];
             caxpy_sub(vh.x, vh.y, vl.x, vl.y, c, ar0, ai0);
             caxpy_sub(vh.z, vh.w, vl.z, vl.w, c, ar1, ai1);
+            vh = nh;
+            vl = nl;
         }
         renorm(ar0); renorm(ai0); renorm(ar1); renorm(ai1);
         wh[q] = make_float4(ar0.hi, ai0.hi, ar1.hi, ai1.hi);
@@ -248,18 +291,41 @@ update_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double
     const double s_ = dfwarp_sum(nr);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s_;
     __syncthreads();
-    if (threadIdx.x == 0 && nrm_partials) {
+    if (!nrm_partials) return;
+    if (threadIdx.x == 0) {
         double t = 0.0;
 #pragma unroll
         for (int k = 0; k < NW; ++k) t += red[k];
         nrm_partials[blockIdx.x] = t;
     }
+    // last CTA: ||w||^2 = sum over CTAs in CTA order (and bump the pass counter)
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    double t = 0.0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += 32) t += __ldcg(nrm_partials + k);
+    t = dwarp_sum(t);
+    if (threadIdx.x == 0) {
+        *nrm2 = t;
+        if (counter) *counter += 1.0;
+        *ticket = 0u;
+    }
 }
 
 // v <- v / sqrt(*nrm2) in df32 (both planes).
 __global__ void scale_df_kernel(int64_t n, float2 *__restrict__ v, const double *__restrict__ nrm2) {
-    const double sd = 1.0 / sqrt(*nrm2);
-    const float sh = (float)sd, sl = (float)(sd - (double)sh);
+    __shared__ float s_sh[2];     // split of 1/sqrt, once per CTA (FP64 division is slow here)
+    if (threadIdx.x == 0) {
+        const double sd = 1.0 / sqrt(*nrm2);
+        s_sh[0] = (float)sd;
+        s_sh[1] = (float)(sd - (double)s_sh[0]);
+    }
+    __syncthreads();
+    const float sh = s_sh[0], sl = s_sh[1];
     float2 *vh = v, *vl = v + n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float2 a = vh[i], al = vl[i];
@@ -279,7 +345,10 @@ __global__ void scale_df_kernel(int64_t n, float2 *__restrict__ v, const double 
 // dst (df32) <- src (FP64) / sqrt(*nrm2): the restart vector of a cycle.
 __global__ void split_f64_df_kernel(int64_t n, const double2 *__restrict__ src, const double *__restrict__ nrm2,
                                     float2 *__restrict__ dst) {
-    const double sc = 1.0 / sqrt(*nrm2);
+    __shared__ double s_sh;
+    if (threadIdx.x == 0) s_sh = 1.0 / sqrt(*nrm2);
+    __syncthreads();
+    const double sc = s_sh;
     float2 *dh = dst, *dl = dst + n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double2 a = src[i];
@@ -290,23 +359,30 @@ __global__ void split_f64_df_kernel(int64_t n, const double2 *__restrict__ src, 
     }
 }
 
-// x (FP64) <- x + sum_j V_j y_j with V in df32 and y in FP64 (end of a cycle).
+// x (FP64) <- x + sum_j V_j y_j with V in df32 and y in FP64 (end of a
+// cycle): the sum runs in df32 (y split once per CTA), one conversion per entry.
 __global__ void __launch_bounds__(DF_THREADS)
 combine_df_kernel(int64_t n, int k, const float2 *__restrict__ V, const double2 *__restrict__ y,
                   double2 *__restrict__ x) {
-    __shared__ double2 ys[DST_MAX_VEC];
-    for (int j = threadIdx.x; j < k; j += DF_THREADS) ys[j] = y[j];
+    __shared__ float4 ys[DST_MAX_VEC];    // -y split: (re_hi, re_lo, im_hi, im_lo)
+    for (int j = threadIdx.x; j < k; j += DF_THREADS) {
+        const double2 c = y[j];
+        const float rh = (float)(-c.x), ih = (float)(-c.y);
+        ys[j] = make_float4(rh, (float)(-c.x - (double)rh), ih, (float)(-c.y - (double)ih));
+    }
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 acc = x[i];
+        DfAcc ar, ai;
+        ar.zero();
+        ai.zero();
         for (int j = 0; j < k; ++j) {
             const float2 *vj = V + (int64_t)j * 2 * n;
             const float2 vh = vj[i], vl = vj[n + i];
-            const double vr = (double)vh.x + (double)vl.x, vi = (double)vh.y + (double)vl.y;
-            const double2 c = ys[j];
-            acc.x = fma(vr, c.x, fma(-vi, c.y, acc.x));
-            acc.y = fma(vr, c.y, fma(vi, c.x, acc.y));
+            caxpy_sub(vh.x, vh.y, vl.x, vl.y, ys[j], ar, ai);     // acc -= v (-y) = acc + v y
         }
+        double2 acc = x[i];
+        acc.x += ar.value();
+        acc.y += ai.value();
         x[i] = acc;
     }
 }
@@ -322,27 +398,30 @@ static unsigned df_stream_blocks(int64_t n) {
 }
 
 int dst_k_project_df(int64_t n, int nvec, const float2 *V, const float2 *w, bool w_hi_only, double2 *h,
-                     double2 *partials, int nblk, cudaStream_t s, double *wnrm2, double *wnrm_partials) {
+                     double2 *partials, int nblk, cudaStream_t s, double *wnrm2, double *wnrm_partials,
+                     const double *gate, unsigned *ticket) {
     if (n & 1) return DST_ERR_ARG;     // two entries per 16-byte load
     if (w_hi_only)
-        project_df_kernel<true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wnrm2 ? wnrm_partials : nullptr);
+        project_df_kernel<true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wnrm2 ? wnrm_partials : nullptr,
+                                                            gate, h, wnrm2, ticket);
     else
-        project_df_kernel<false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wnrm2 ? wnrm_partials : nullptr);
+        project_df_kernel<false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wnrm2 ? wnrm_partials : nullptr,
+                                                             gate, h, wnrm2, ticket);
     DST_CUDA_TRY(cudaGetLastError());
-    int rc = dst_k_reduce_partials(nblk, nvec, partials, h, s);
-    if (rc == DST_OK && wnrm2) rc = dst_k_reduce_real(nblk, wnrm_partials, wnrm2, s);
-    return rc;
+    return DST_OK;
 }
 
 int dst_k_update_df(int64_t n, int nvec, const float2 *V, const double2 *h, float2 *w, bool w_hi_only, double *nrm2,
-                    double *partials, int nblk, cudaStream_t s) {
+                    double *partials, int nblk, cudaStream_t s, const double *gate, double *counter,
+                    unsigned *ticket) {
     if (n & 1) return DST_ERR_ARG;
     if (w_hi_only)
-        update_df_kernel<true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, nrm2 ? partials : nullptr);
+        update_df_kernel<true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, nrm2 ? partials : nullptr, gate, nrm2,
+                                                           counter, ticket);
     else
-        update_df_kernel<false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, nrm2 ? partials : nullptr);
+        update_df_kernel<false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, nrm2 ? partials : nullptr, gate, nrm2,
+                                                            counter, ticket);
     DST_CUDA_TRY(cudaGetLastError());
-    if (nrm2) return dst_k_reduce_real(nblk, partials, nrm2, s);
     return DST_OK;
 }
 

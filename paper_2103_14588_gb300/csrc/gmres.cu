@@ -39,6 +39,7 @@ struct Workspace {
     double2 *V, *b, *tmp, *d, *r64, *h1, *h2;
     float2 *x32, *y32;
     double *nrm;
+    unsigned *tickets;     // [2] zero counters of the in-kernel reductions
     double2 *partials_c;
     double *partials_r;
     double *host;      // pinned, 2 * 2 * (m + 1) + 8 doubles
@@ -62,6 +63,7 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w) {
     const size_t oh1 = take(sizeof(double2) * DST_MAX_VEC);
     const size_t oh2 = take(sizeof(double2) * DST_MAX_VEC);
     const size_t onrm = take(sizeof(double) * 8);
+    const size_t otk = take(sizeof(unsigned) * 8);
     const size_t opc = take(sizeof(double2) * (size_t)nblk * DST_MAX_VEC);
     const size_t opr = take(sizeof(double) * (size_t)nblk);
     const size_t total = off;
@@ -91,6 +93,7 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w) {
     w.h1 = (double2 *)(base + oh1);
     w.h2 = (double2 *)(base + oh2);
     w.nrm = (double *)(base + onrm);
+    w.tickets = (unsigned *)(base + otk);
     w.partials_c = (double2 *)(base + opc);
     w.partials_r = (double *)(base + opr);
     return DST_OK;
@@ -186,7 +189,8 @@ struct Solver {
     dst_mesh *mesh;
     cudaStream_t s;
     Workspace w;
-    int nblk;
+    int nblk;         // CTAs of the reduction / update passes
+    int nblk_proj;    // CTAs of the df32 projection (fewer, longer slices)
     double bytes = 0.0;
     int iters = 0;
     int restarts = 0;
@@ -224,15 +228,31 @@ struct Solver {
         if (rc) return rc;
         return run(K_CAST, 1, 24.0 * n, 0.0, [&] { return dst_k_cast_32_64(w.n, w.y32, out, s); });
     }
-    int project(int nv, const double2 *wv, double2 *h, double *wnrm2 = nullptr) {
+    // gate: second-pass kernels that skip themselves on the device when the
+    // DGKS test (nrm[0] < nrm[3] / 2) fails; their bytes are counted only if
+    // they ran (second_pass_ran() after the step's synchronisation).
+    int project(int nv, const double2 *wv, double2 *h, double *wnrm2 = nullptr, const double *gate = nullptr) {
         const double n = (double)w.n;
-        return run(K_PROJECT, wnrm2 ? 3 : 2, 16.0 * n * (nv + 1), 8.0 * n * nv + (wnrm2 ? 4.0 * n : 0.0),
-                   [&] { return dst_k_project(w.n, nv, w.V, wv, h, w.partials_c, nblk, s, wnrm2, w.partials_r); });
+        return run(K_PROJECT, wnrm2 ? 3 : 2, gate ? 0.0 : 16.0 * n * (nv + 1),
+                   gate ? 0.0 : 8.0 * n * nv + (wnrm2 ? 4.0 * n : 0.0),
+                   [&] { return dst_k_project(w.n, nv, w.V, wv, h, w.partials_c, nblk, s, wnrm2, w.partials_r, gate); });
     }
-    int update(int nv, const double2 *h, double2 *x, double *nrm2) {
+    // second: the step's second Gram-Schmidt pass (bumps the device counter nrm[6] when it runs)
+    int update(int nv, const double2 *h, double2 *x, double *nrm2, const double *gate = nullptr, bool second = false) {
         const double n = (double)w.n;
-        return run(K_UPDATE, nrm2 ? 2 : 1, 16.0 * n * (nv + 2), 8.0 * n * nv + (nrm2 ? 4.0 * n : 0.0),
-                   [&] { return dst_k_update(w.n, nv, w.V, h, x, nrm2, w.partials_r, nblk, s); });
+        return run(K_UPDATE, nrm2 ? 2 : 1, gate ? 0.0 : 16.0 * n * (nv + 2),
+                   gate ? 0.0 : 8.0 * n * nv + (nrm2 ? 4.0 * n : 0.0),
+                   [&] { return dst_k_update(w.n, nv, w.V, h, x, nrm2, w.partials_r, nblk, s, gate,
+                                             second ? w.nrm + 6 : nullptr); });
+    }
+    // account a gated second pass over nv basis vectors that did run
+    void count_second_pass(int nv, bool df) {
+        const double n = (double)w.n;
+        const double pb = df ? 16.0 * n * (nv + 1) : 16.0 * n * (nv + 1);
+        const double ub = 16.0 * n * (nv + 2);
+        prof.bytes[K_PROJECT] += pb; prof.flops[K_PROJECT] += 8.0 * n * nv;
+        prof.bytes[K_UPDATE] += ub; prof.flops[K_UPDATE] += 8.0 * n * nv;
+        bytes += pb + ub;
     }
     int scale(double2 *v) {
         return run(K_SCALE, 1, 32.0 * w.n, 2.0 * w.n, [&] { return dst_k_scale(w.n, v, v, w.nrm, 0.0, s); });
@@ -277,6 +297,24 @@ struct Solver {
         beta = std::sqrt(w.host[0]);
         return DST_OK;
     }
+
+    // One host synchronisation per Arnoldi step: both Gram-Schmidt columns and
+    // the norms / second-pass counter (nrm[0..7]) come back together.
+    double reorth_seen = 0.0;
+    bool last_second = false;
+    int read_step(int nv) {
+        DST_CUDA_TRY(cudaMemcpyAsync(w.host, w.h1, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
+        DST_CUDA_TRY(cudaMemcpyAsync(w.host + 2 * DST_MAX_VEC, w.h2, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
+        DST_CUDA_TRY(cudaMemcpyAsync(w.host + 4 * DST_MAX_VEC, w.nrm, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        int rc = sync();
+        if (rc) return rc;
+        const double cnt = w.host[4 * DST_MAX_VEC + 6];
+        last_second = cnt > reorth_seen;
+        reorth_seen = cnt;
+        if (last_second) ++reorths;
+        return DST_OK;
+    }
+    bool second_pass_ran() const { return last_second; }
 
     // Hessenberg column j from the host buffer (first pass at host[0], second
     // pass at host[2*MAXVEC], new norm^2 at host[4*MAXVEC]) into hs; returns
@@ -323,26 +361,13 @@ struct Solver {
                 // classical Gram-Schmidt pass; ||A v_j||^2 (before) into nrm[3], ||w||^2 (after) into nrm[0]
                 if ((rc = project(nv, wv, w.h1, w.nrm + 3))) return rc;
                 if ((rc = update(nv, w.h1, wv, w.nrm))) return rc;
-                DST_CUDA_TRY(cudaMemcpyAsync(w.host, w.h1, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
-                DST_CUDA_TRY(cudaMemcpyAsync(w.host + 4 * DST_MAX_VEC, w.nrm, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-                bool second = ortho == 1;
-                if (!second) {
-                    if ((rc = sync())) return rc;
-                    second = w.host[4 * DST_MAX_VEC] < 0.5 * w.host[4 * DST_MAX_VEC + 3];   // DGKS
-                }
-                if (second) {
-                    ++reorths;
-                    if ((rc = project(nv, wv, w.h2))) return rc;
-                    if ((rc = update(nv, w.h2, wv, w.nrm))) return rc;
-                    DST_CUDA_TRY(cudaMemcpyAsync(w.host + 2 * DST_MAX_VEC, w.h2, sizeof(double2) * nv,
-                                                 cudaMemcpyDeviceToHost, s));
-                    DST_CUDA_TRY(cudaMemcpyAsync(w.host + 4 * DST_MAX_VEC, w.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
-                } else {
-                    for (int i = 0; i < 2 * nv; ++i) w.host[2 * DST_MAX_VEC + i] = 0.0;
-                }
-                // normalise on the device (1/sqrt(nrm)), then read the column
-                if ((rc = scale(wv))) return rc;
-                if ((rc = sync())) return rc;
+                // second pass, gated on the device by the DGKS test unless always on (CGS2)
+                const double *gate = ortho == 1 ? nullptr : w.nrm;
+                if ((rc = project(nv, wv, w.h2, nullptr, gate))) return rc;
+                if ((rc = update(nv, w.h2, wv, w.nrm, gate, true))) return rc;
+                if ((rc = scale(wv))) return rc;     // normalise on the device (1/sqrt(nrm))
+                if ((rc = read_step(nv))) return rc;
+                if (second_pass_ran() && gate) count_second_pass(nv, false);
                 ++iters;
                 if ((rc = take_column(hs, j, breakdown))) return rc;
                 k = j + 1;
@@ -387,37 +412,28 @@ struct Solver {
             if ((rc = run(K_APPLY32, 1, 16.0 * dn, 0.0,
                           [&] { return dst_internal_apply(mesh, DST_FP32, vj, wv, s); })))
                 return rc;
-            if ((rc = run(K_PROJECT, 3, 16.0 * dn * nv + 8.0 * dn, 8.0 * dn * nv,
-                          [&] { return dst_k_project_df(n, nv, Vd, wv, true, w.h1, w.partials_c, nblk, s, w.nrm + 3,
-                                                        w.partials_r); })))
+            if ((rc = run(K_PROJECT, 1, 16.0 * dn * nv + 8.0 * dn, 8.0 * dn * nv,
+                          [&] { return dst_k_project_df(n, nv, Vd, wv, true, w.h1, w.partials_c, nblk_proj, s,
+                                                        w.nrm + 3, w.partials_r, nullptr, w.tickets); })))
                 return rc;
-            if ((rc = run(K_UPDATE, 2, 16.0 * dn * nv + 24.0 * dn, 8.0 * dn * nv,
-                          [&] { return dst_k_update_df(n, nv, Vd, w.h1, wv, true, w.nrm, w.partials_r, nblk, s); })))
+            if ((rc = run(K_UPDATE, 1, 16.0 * dn * nv + 24.0 * dn, 8.0 * dn * nv,
+                          [&] { return dst_k_update_df(n, nv, Vd, w.h1, wv, true, w.nrm, w.partials_r, nblk, s,
+                                                       nullptr, nullptr, w.tickets + 1); })))
                 return rc;
-            DST_CUDA_TRY(cudaMemcpyAsync(w.host, w.h1, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
-            DST_CUDA_TRY(cudaMemcpyAsync(w.host + 4 * DST_MAX_VEC, w.nrm, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-            bool second = ortho == 1;
-            if (!second) {
-                if ((rc = sync())) return rc;
-                second = w.host[4 * DST_MAX_VEC] < 0.5 * w.host[4 * DST_MAX_VEC + 3];   // DGKS
-            }
-            if (second) {
-                ++reorths;
-                if ((rc = run(K_PROJECT, 2, 16.0 * dn * (nv + 1), 8.0 * dn * nv,
-                              [&] { return dst_k_project_df(n, nv, Vd, wv, false, w.h2, w.partials_c, nblk, s, nullptr,
-                                                            nullptr); })))
-                    return rc;
-                if ((rc = run(K_UPDATE, 2, 16.0 * dn * (nv + 2), 8.0 * dn * nv,
-                              [&] { return dst_k_update_df(n, nv, Vd, w.h2, wv, false, w.nrm, w.partials_r, nblk, s); })))
-                    return rc;
-                DST_CUDA_TRY(cudaMemcpyAsync(w.host + 2 * DST_MAX_VEC, w.h2, sizeof(double2) * nv,
-                                             cudaMemcpyDeviceToHost, s));
-                DST_CUDA_TRY(cudaMemcpyAsync(w.host + 4 * DST_MAX_VEC, w.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
-            } else {
-                for (int i = 0; i < 2 * nv; ++i) w.host[2 * DST_MAX_VEC + i] = 0.0;
-            }
+            // second pass, gated on the device by the DGKS test unless always on (CGS2)
+            const double *gate = ortho == 1 ? nullptr : w.nrm;
+            const double g2 = gate ? 0.0 : 1.0;
+            if ((rc = run(K_PROJECT, 1, g2 * 16.0 * dn * (nv + 1), g2 * 8.0 * dn * nv,
+                          [&] { return dst_k_project_df(n, nv, Vd, wv, false, w.h2, w.partials_c, nblk_proj, s,
+                                                        nullptr, nullptr, gate, w.tickets); })))
+                return rc;
+            if ((rc = run(K_UPDATE, 1, g2 * 16.0 * dn * (nv + 2), g2 * 8.0 * dn * nv,
+                          [&] { return dst_k_update_df(n, nv, Vd, w.h2, wv, false, w.nrm, w.partials_r, nblk, s, gate,
+                                                       w.nrm + 6, w.tickets + 1); })))
+                return rc;
             if ((rc = run(K_SCALE, 1, 32.0 * dn, 6.0 * dn, [&] { return dst_k_scale_df(n, wv, w.nrm, s); }))) return rc;
-            if ((rc = sync())) return rc;
+            if ((rc = read_step(nv))) return rc;
+            if (second_pass_ran() && gate) count_second_pass(nv, true);
             ++iters;
             if ((rc = take_column(hs, j, breakdown))) return rc;
             k = j + 1;
@@ -458,6 +474,7 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     sv.mesh = mesh;
     sv.s = s;
     sv.nblk = dst_reduction_blocks(mesh->n_unknowns);
+    sv.nblk_proj = dst_projection_blocks(mesh->n_unknowns);
     sv.ortho = o.ortho;
     int rc = setup_workspace(mesh, o.restart, mixed, sv.w);
     if (rc) return rc;
@@ -472,6 +489,8 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     const int64_t n = mesh->n_unknowns;
     // b = -D_w21 psi0 and ||b||
     sv.prof.on = o.profile != 0;
+    DST_CUDA_TRY(cudaMemsetAsync(sv.w.nrm, 0, 8 * sizeof(double), s));
+    DST_CUDA_TRY(cudaMemsetAsync(sv.w.tickets, 0, 8 * sizeof(unsigned), s));
     if ((rc = sv.run(K_RHS, 1, 16.0 * n + 16.0 * mesh->n_spatial * mesh->nc, 0.0,
                      [&] { return dst_internal_rhs(mesh, sv.w.b, s); })))
         return rc;
