@@ -140,7 +140,7 @@ __device__ __forceinline__ void fields(Get get, const NodeCoef<D, T> &k, typenam
         wx[sb][1] = k.wl[sb] * k.cx.ml[1] + k.wr[sb] * k.cx.mr[1];
         wx[sb][2] = k.wr[sb] * k.cx.mr[2];
     }
-#pragma unroll (D >= 3 ? 1 : 3)
+#pragma unroll
     for (int dz = 0; dz < NZ; ++dz) {
         V pM[NC], pCx[NC], pCy[NC], pW[NC];
 #pragma unroll
@@ -201,7 +201,7 @@ __device__ __forceinline__ void fields_nov(Get get, const NodeCoef<D, T> &k, T m
     V sM[NC], sCx[NC], sCy[NC], sCz[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) { sM[c] = cz<V>(); sCx[c] = cz<V>(); sCy[c] = cz<V>(); sCz[c] = cz<V>(); }
-#pragma unroll (D >= 3 ? 1 : 3)
+#pragma unroll
     for (int dz = 0; dz < NZ; ++dz) {
         V pM[NC], pCx[NC], pCy[NC];
 #pragma unroll

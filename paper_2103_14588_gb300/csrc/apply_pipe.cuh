@@ -36,7 +36,10 @@ struct PipeShape {
     static constexpr int NODE_BYTES = NC * 2 * (int)sizeof(T);        // 16, 32 or 64
     static constexpr int CHUNKS = NODE_BYTES / 16;                    // 16-byte copies per node
     static constexpr int NTHR = Tile::TX * Tile::TY * Tile::TZ;
-    static constexpr int STAGES = (BOX * NODE_BYTES * 4 <= 96 * 1024) ? 4 : 3;
+    // two planes per step (twice the independent work per barrier) when a
+    // six-plane ring fits comfortably; otherwise one plane per step, 4 or 3 stages
+    static constexpr bool PAIR = BOX * NODE_BYTES * 8 <= 72 * 1024;
+    static constexpr int STAGES = PAIR ? 8 : ((BOX * NODE_BYTES * 4 <= 96 * 1024) ? 4 : 3);
     static constexpr int SMEM = STAGES * BOX * NODE_BYTES;
 };
 
@@ -173,7 +176,7 @@ __device__ __forceinline__ void fields_std(Get get, const StdConst<T> &sc, T m, 
     V QM[NC], QCx[NC], QCy[NC], QCz[NC], QW[NC];   // sums over z of [1,4,1] (and [-1,0,1] for z)
 #pragma unroll
     for (int c = 0; c < NC; ++c) { QM[c] = cz<V>(); QCx[c] = cz<V>(); QCy[c] = cz<V>(); QCz[c] = cz<V>(); QW[c] = cz<V>(); }
-#pragma unroll (D >= 3 ? 1 : 3)
+#pragma unroll
     for (int dz = 0; dz < NZ; ++dz) {
         V PM[NC], PCx[NC], PCy[NC], PW[NC];
 #pragma unroll
@@ -231,7 +234,7 @@ __device__ __forceinline__ void fields_std(Get get, const StdConst<T> &sc, T m, 
 }
 
 template <int D, int NC, typename T, bool NOV>
-__global__ void __launch_bounds__(PipeShape<D, NC, T>::NTHR)
+__global__ void __launch_bounds__(PipeShape<D, NC, T>::NTHR, (D == 3 || sizeof(T) == 8) ? 1 : 3)
 apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typename C2<T>::type *__restrict__ y,
                   int64_t tiles_x, int64_t tiles_y) {
     using V = typename C2<T>::type;
@@ -280,31 +283,29 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
     const int NY = D >= 2 ? 3 : 1;
     const int c0 = (tz * S::BY + ty) * S::BX + tx;      // box index of the (-1,-1,-1) neighbour
 
-    auto issue = [&](int i) {
-        const int64_t pl = pfirst + i;
-        if (pl >= 1 && pl <= N)
-            issue_plane<D, NC, T>(cplan, reinterpret_cast<const char *>(x + (pl - 1) * plane_elems),
-                                  ring + (size_t)(i % S::STAGES) * S::BOX * S::NODE_BYTES);
+    // Plane-loop bookkeeping in 32-bit, relative to the chunk: plane i is time
+    // layer pfirst + i; it exists iff i_lo <= i <= i_hi; outputs are stored
+    // for i >= 2; the final layer's diagonal applies for i >= i_last.
+    const int i_lo = (int)max((int64_t)0, 1 - pfirst);
+    const int i_hi = (int)min((int64_t)(nplanes - 1), N - pfirst);
+    const int i_last = (int)(N - pfirst);
+    const size_t plane_bytes = (size_t)plane_elems * sizeof(V);
+    const size_t slot_bytes = (size_t)S::BOX * S::NODE_BYTES;
+    const char *xsrc = reinterpret_cast<const char *>(x) + (pfirst - 1) * (int64_t)plane_bytes;   // plane i = xsrc + i*plane_bytes
+    char *ydst = reinterpret_cast<char *>(y + (t0 - 1) * plane_elems + self * NC);               // layer t0
+    int issue_slot = 0;
+    const char *issue_src = xsrc;
+
+    auto issue_next = [&](int i) {      // plane i into the next ring slot (i strictly increasing)
+        if (i >= i_lo && i <= i_hi) issue_plane<D, NC, T>(cplan, issue_src, ring + (size_t)issue_slot * slot_bytes);
         cp_async_commit();
+        issue_src += plane_bytes;
+        issue_slot = issue_slot + 1 == S::STAGES ? 0 : issue_slot + 1;
     };
-#pragma unroll
-    for (int i = 0; i < S::STAGES - 1; ++i)
-        if (i < nplanes) issue(i); else cp_async_commit();
-
-    V accP[NC], accC[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) { accP[c] = cz<V>(); accC[c] = cz<V>(); }
-
-    for (int i = 0; i < nplanes; ++i) {
-        cp_async_wait<S::STAGES - 2>();
-        __syncthreads();
-        if (i + S::STAGES - 1 < nplanes) issue(i + S::STAGES - 1); else cp_async_commit();
-        const int64_t pl = pfirst + i;
-        const bool have = pl >= 1 && pl <= N;
-        // G_C' = G_C / 2 and G_M' = (h_t / 6) G_M of this plane
-        V GC[NC], GM[NC];
-        if (have && valid) {
-            const char *slot = ring + (size_t)(i % S::STAGES) * S::BOX * S::NODE_BYTES;
+    // G_C' = G_C / 2 and G_M' = (h_t / 6) G_M of plane i held in ring slot si
+    auto plane_fields = [&](int i, int si, V *GC, V *GM) {
+        if (i >= i_lo && i <= i_hi && valid) {
+            const char *slot = ring + (size_t)si * slot_bytes;
             auto get = [&](int r) {
                 const int dz = r / (3 * NY), dy = (r / 3) % NY, dx = r % 3;
                 return smem_node<NC, T>(slot, c0 + (dz * S::BY + dy) * S::BX + dx);
@@ -321,19 +322,60 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
 #pragma unroll
             for (int c = 0; c < NC; ++c) { GC[c] = cz<V>(); GM[c] = cz<V>(); }
         }
-        // y(pl-1) += G_C' + G_M'; y(pl) += (pl < N ? 4 G_M' : G_C' + 2 G_M'); y(pl+1) = G_M' - G_C'
-        const bool last = pl >= N;
+    };
+
+    V accP[NC], accC[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { accP[c] = cz<V>(); accC[c] = cz<V>(); }
+    // y(pl-1) += G_C' + G_M'; y(pl) += (pl < N ? 4 G_M' : G_C' + 2 G_M'); y(pl+1) = G_M' - G_C'
+    auto accumulate = [&](int i, const V *GC, const V *GM) {
+        const bool last = i >= i_last;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             accP[c] = cadd(accP[c], cadd(GC[c], GM[c]));
             if (last) accC[c] = cadd(accC[c], cfma_r((T)2, GM[c], GC[c]));
             else accC[c] = cfma_r((T)4, GM[c], accC[c]);
         }
-        if (valid && pl - 1 >= t0 && pl - 1 < t1) store_node<NC, T>(y + (pl - 2) * plane_elems, self, accP);
+        if (valid && i >= 2) {
+            store_node<NC, T>(reinterpret_cast<V *>(ydst), 0, accP);
+            ydst += plane_bytes;
+        }
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             accP[c] = accC[c];
             accC[c] = csub(GM[c], GC[c]);
+        }
+    };
+
+    if (S::PAIR) {
+        // ring of 8: planes i, i+1 computed while up to six more are in flight
+#pragma unroll
+        for (int i = 0; i < S::STAGES - 2; ++i) issue_next(i);
+        int si = 0;
+        for (int i = 0; i < nplanes; i += 2) {
+            cp_async_wait<S::STAGES - 4>();
+            __syncthreads();
+            issue_next(i + S::STAGES - 2);
+            issue_next(i + S::STAGES - 1);
+            V GC0[NC], GM0[NC], GC1[NC], GM1[NC];
+            plane_fields(i, si, GC0, GM0);
+            plane_fields(i + 1, si + 1, GC1, GM1);
+            si = (si + 2) & (S::STAGES - 1);
+            accumulate(i, GC0, GM0);
+            if (i + 1 < nplanes) accumulate(i + 1, GC1, GM1);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < S::STAGES - 1; ++i) issue_next(i);
+        int si = 0;
+        for (int i = 0; i < nplanes; ++i) {
+            cp_async_wait<S::STAGES - 2>();
+            __syncthreads();
+            issue_next(i + S::STAGES - 1);
+            V GC[NC], GM[NC];
+            plane_fields(i, si, GC, GM);
+            si = si + 1 == S::STAGES ? 0 : si + 1;
+            accumulate(i, GC, GM);
         }
     }
     cp_async_wait<0>();
