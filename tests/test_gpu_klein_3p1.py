@@ -1,0 +1,47 @@
+"""Full-size 3+1 Klein-step solve (48^3 x 48, 20,791,296 complex unknowns), checked element by element.
+
+The workload's initial packet and step potential depend on x only and the
+y, z axes are periodic, so the discrete 3+1 solution reduces exactly to 1+1
+(component pairs (psi_1, psi_4) and (psi_2, psi_3) each obey the 1+1 system,
+the cross-dimension reduction pinned in tests/test_oracle_operator.py).  The
+oracle solves that 1+1 system by LU on the x-t mesh (47 x 48 nodes); every
+(y, z) column of the GPU's mixed-precision solution must match it to the
+refinement tolerance (rel. L2 <= 1e-8 after solving to 1e-11).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_klein_3p1_full_size_matches_1p1_oracle():
+    import torch
+    from oracle import mesh as OM, operator as OOP, solvers as OS
+    from paper_2103_14588_gb300 import binding as B
+    w = W.klein_3p1(p0=1.05)
+    with B.Mesh.from_workload(w) as mesh:
+        assert mesh.n_unknowns == 20791296
+        psi = torch.zeros(mesh.n_unknowns, dtype=torch.complex128, device="cuda")
+        st = B.dst_solve(mesh.handle, {"restart": 30, "rtol": 1e-11, "max_iters": 20000, "mixed_precision": 1}, psi)
+        torch.cuda.synchronize()
+        assert st["status"] == 0, st
+        sol = psi.view(48, 48, 48, 47, 4).cpu().numpy()
+    # 1+1 oracle on the x-t mesh: same x axis (Dirichlet, 48 elements on [-6, 6]), same t axis
+    m1 = OM.Mesh(1, [48, 1, 1, 48], [-6.0, 0, 0, 0.0], [6.0, 1, 1, 3.0], [W.DIRICHLET, 0, 0])
+    Vx = w.V.reshape(48, 48, 48)[0, 0, :]
+    pz = w.psi0[0, 0]                       # (47, 4), identical for every (z, y)
+    A, b = OOP.split(m1, OOP.assemble(m1, w.m, Vx), pz[:, [0, 3]])
+    s14 = OS.sparse_solve(A, b).reshape(48, 47, 2)
+    A, b = OOP.split(m1, OOP.assemble(m1, w.m, Vx), pz[:, [1, 2]])
+    s23 = OS.sparse_solve(A, b).reshape(48, 47, 2)
+    ref = np.zeros((48, 47, 4), dtype=complex)
+    ref[..., 0], ref[..., 3] = s14[..., 0], s14[..., 1]
+    ref[..., 1], ref[..., 2] = s23[..., 0], s23[..., 1]
+    nref = np.linalg.norm(ref)
+    worst = 0.0
+    for iz in range(48):
+        for iy in range(48):
+            worst = max(worst, np.linalg.norm(sol[:, iz, iy] - ref) / nref)
+    assert worst <= 1e-8, worst

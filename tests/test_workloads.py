@@ -41,4 +41,4 @@ def test_klein_potential_step():
     w = W.klein_3p1(n=8, nt=4, p0=1.05)
     V = w.V.reshape(8, 8, 8)
     assert np.all(V[:, :, :4] == 0.0) and np.all(V[:, :, 4:] == 2.5)
-    assert w.psi0.shape == (8, 8, 9, 4)
+    assert w.psi0.shape == (8, 8, 7, 4)
