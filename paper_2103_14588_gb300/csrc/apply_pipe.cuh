@@ -21,10 +21,13 @@
 
 namespace dst {
 
+// Output tile TX x TY x TZ per CTA and TT time layers; each thread computes RY
+// consecutive y outputs (2+1: the x stencils of the rows they share are
+// computed once).
 template <int D> struct PipeTile;
-template <> struct PipeTile<1> { static constexpr int TX = 256, TY = 1, TZ = 1, TT = 32; };
-template <> struct PipeTile<2> { static constexpr int TX = 32, TY = 8, TZ = 1, TT = 8; };
-template <> struct PipeTile<3> { static constexpr int TX = 16, TY = 4, TZ = 4, TT = 8; };
+template <> struct PipeTile<1> { static constexpr int TX = 256, TY = 1, TZ = 1, TT = 32, RY = 1; };
+template <> struct PipeTile<2> { static constexpr int TX = 32, TY = 8, TZ = 1, TT = 8, RY = 2; };
+template <> struct PipeTile<3> { static constexpr int TX = 16, TY = 4, TZ = 4, TT = 8, RY = 1; };
 
 template <int D, int NC, typename T>
 struct PipeShape {
@@ -35,10 +38,11 @@ struct PipeShape {
     static constexpr int BOX = BX * BY * BZ;                          // nodes per staged plane
     static constexpr int NODE_BYTES = NC * 2 * (int)sizeof(T);        // 16, 32 or 64
     static constexpr int CHUNKS = NODE_BYTES / 16;                    // 16-byte copies per node
-    static constexpr int NTHR = Tile::TX * Tile::TY * Tile::TZ;
-    // two planes per step (twice the independent work per barrier) when a
-    // six-plane ring fits comfortably; otherwise one plane per step, 4 or 3 stages
-    static constexpr bool PAIR = BOX * NODE_BYTES * 8 <= 72 * 1024;
+    static constexpr int NTHR = Tile::TX * (Tile::TY / Tile::RY) * Tile::TZ;
+    // two planes per step (twice the independent work per barrier) when one
+    // output per thread and an eight-plane ring fits comfortably; otherwise one
+    // plane per step, 4 or 3 stages
+    static constexpr bool PAIR = Tile::RY == 1 && BOX * NODE_BYTES * 8 <= 72 * 1024;
     static constexpr int STAGES = PAIR ? 8 : ((BOX * NODE_BYTES * 4 <= 96 * 1024) ? 4 : 3);
     static constexpr int SMEM = STAGES * BOX * NODE_BYTES;
 };
@@ -233,6 +237,50 @@ __device__ __forceinline__ void fields_std(Get get, const StdConst<T> &sc, T m, 
     if (D >= 3) add_i_alpha<NC>(2, sc.ka[2], QCz, GM);
 }
 
+// 2+1, standard interior stencils, RY consecutive y outputs of one thread:
+// the x stencils of the RY + 2 rows are computed once and shared.
+// get(q, dx): node of row q (0 .. RY+1) and column dx (0 .. 2).
+template <int NC, typename T, bool WV, int RY, typename Get>
+__device__ __forceinline__ void fields_std_rows(Get get, const StdConst<T> &sc, T m, const T (&wx)[2][3],
+                                                typename C2<T>::type (*GC)[NC], typename C2<T>::type (*GM)[NC]) {
+    using V = typename C2<T>::type;
+    V rM[RY + 2][NC], rC[RY + 2][NC], rW[WV ? RY + 2 : 1][NC];
+#pragma unroll
+    for (int q = 0; q < RY + 2; ++q) {
+        const NodeV<NC, T> n0 = get(q, 0), n1 = get(q, 1), n2 = get(q, 2);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const V x0 = n0.c[c], x1 = n1.c[c], x2 = n2.c[c];
+            rM[q][c].x = fma((T)4, x1.x, x0.x + x2.x); rM[q][c].y = fma((T)4, x1.y, x0.y + x2.y);
+            rC[q][c].x = x2.x - x0.x; rC[q][c].y = x2.y - x0.y;
+            if (WV) {
+                const int sb = Beta<2>::s(c) > 0 ? 0 : 1;
+                rW[WV ? q : 0][c] = cfma_r(wx[sb][0], x0, cfma_r(wx[sb][1], x1, cmul_r(wx[sb][2], x2)));
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        V PM[NC], PCx[NC], PCy[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            PM[c] = cfma_r((T)4, rM[r + 1][c], cadd(rM[r][c], rM[r + 2][c]));
+            PCx[c] = cfma_r((T)4, rC[r + 1][c], cadd(rC[r][c], rC[r + 2][c]));
+            PCy[c] = csub(rM[r + 2][c], rM[r][c]);
+            GC[r][c].x = -sc.kc * PM[c].y; GC[r][c].y = sc.kc * PM[c].x;
+            if (WV) {
+                const V PW = cfma_r((T)4, rW[WV ? r + 1 : 0][c], cadd(rW[WV ? r : 0][c], rW[WV ? r + 2 : 0][c]));
+                GM[r][c] = cmul_r(-sc.km, PW);
+            } else {
+                const T f = Beta<2>::s(c) > 0 ? -m * sc.km : m * sc.km;
+                GM[r][c] = cmul_r(f, PM[c]);
+            }
+        }
+        add_i_alpha<NC>(0, sc.ka[0], PCx, GM[r]);
+        add_i_alpha<NC>(1, sc.ka[1], PCy, GM[r]);
+    }
+}
+
 template <int D, int NC, typename T, bool NOV>
 __global__ void __launch_bounds__(PipeShape<D, NC, T>::NTHR, (D == 3 || sizeof(T) == 8) ? 1 : 3)
 apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typename C2<T>::type *__restrict__ y,
@@ -240,6 +288,8 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
     using V = typename C2<T>::type;
     using S = PipeShape<D, NC, T>;
     using Tile = typename S::Tile;
+    constexpr int RY = Tile::RY;
+    constexpr int TYT = Tile::TY / RY;                  // threads along y
     extern __shared__ __align__(16) char ring[];
 
     const int64_t tile = blockIdx.x;
@@ -248,11 +298,10 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
     const int64_t y0 = ((tile / tiles_x) % tiles_y) * Tile::TY;
     const int64_t z0 = (tile / (tiles_x * tiles_y)) * Tile::TZ;
     const int tx = threadIdx.x % Tile::TX;
-    const int ty = (threadIdx.x / Tile::TX) % Tile::TY;
-    const int tz = threadIdx.x / (Tile::TX * Tile::TY);
+    const int ty = ((threadIdx.x / Tile::TX) % TYT) * RY;     // first of the thread's RY output rows
+    const int tz = threadIdx.x / (Tile::TX * TYT);
     const int64_t ix = x0 + tx, iy = y0 + ty, iz = z0 + tz;
     const int64_t nx = p.ax[0].n, ny = p.ax[1].n, nz = p.ax[2].n;
-    const bool valid = ix < nx && iy < ny && iz < nz;
     const int64_t N = p.nt;
     const int64_t t0 = 1 + chunk * Tile::TT;
     const int64_t t1 = min(t0 + (int64_t)Tile::TT, N + 1);
@@ -261,27 +310,41 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
     const int nplanes = (int)(t1 - t0 + 2);            // planes t0-1 .. t1
     const int64_t pfirst = t0 - 1;
 
-    NodeCoef<D, T> k;
-    if (valid) node_coef<D, T>(p, ix, iy, iz, k);
-    // standard interior stencils on every axis (periodic / Dirichlet axes, and
-    // open axes away from their two end nodes)
-    bool stdn = valid;
-    if (valid) {
-        stdn = k.cx.eL && k.cx.eR;
-        if (D >= 2) stdn = stdn && k.cy.eL && k.cy.eR;
-        if (D >= 3) stdn = stdn && k.cz.eL && k.cz.eR;
+    bool valid[RY];
+    bool stdn[RY];
+    bool any_valid = false, all_std = true;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        valid[r] = ix < nx && iy + r < ny && iz < nz;
+        any_valid = any_valid || valid[r];
     }
+    NodeCoef<D, T> k;      // coefficients of output row 0 (x and z are shared by all rows)
+    if (valid[0]) node_coef<D, T>(p, ix, iy, iz, k);
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        // standard interior stencils on every axis (periodic / Dirichlet axes,
+        // and open axes away from their two end nodes)
+        bool sd = valid[r] && k.cx.eL && k.cx.eR;
+        if (D >= 2 && valid[r]) {
+            const Coef3<T> cy = r == 0 ? k.cy : axis_coef<T>(p.ax[1], iy + r);
+            sd = sd && cy.eL && cy.eR;
+        }
+        if (D >= 3) sd = sd && k.cz.eL && k.cz.eR;
+        stdn[r] = sd;
+        all_std = all_std && (sd || !valid[r]);
+    }
+    all_std = all_std && valid[0];
     const StdConst<T> sc = std_const<D, T>(p);
     T wxs[2][3];     // x weights (m beta + V) of the standard path, h_x / 6 folded into StdConst
     for (int sb = 0; sb < 2; ++sb) {
-        const T wl = valid ? k.wl[sb] : (T)0, wr = valid ? k.wr[sb] : (T)0;
+        const T wl = valid[0] ? k.wl[sb] : (T)0, wr = valid[0] ? k.wr[sb] : (T)0;
         wxs[sb][0] = wl; wxs[sb][1] = 2 * (wl + wr); wxs[sb][2] = wr;
     }
     CopyPlan<D, NC, T> cplan;
     make_copy_plan<D, NC, T>(p, x0, y0, z0, cplan);
     const T h6 = (T)(p.ht / 6.0);
     const int NY = D >= 2 ? 3 : 1;
-    const int c0 = (tz * S::BY + ty) * S::BX + tx;      // box index of the (-1,-1,-1) neighbour
+    const int c0 = (tz * S::BY + ty) * S::BX + tx;      // box index of the (-1,-1,-1) neighbour of row 0
 
     // Plane-loop bookkeeping in 32-bit, relative to the chunk: plane i is time
     // layer pfirst + i; it exists iff i_lo <= i <= i_hi; outputs are stored
@@ -292,7 +355,8 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
     const size_t plane_bytes = (size_t)plane_elems * sizeof(V);
     const size_t slot_bytes = (size_t)S::BOX * S::NODE_BYTES;
     const char *xsrc = reinterpret_cast<const char *>(x) + (pfirst - 1) * (int64_t)plane_bytes;   // plane i = xsrc + i*plane_bytes
-    char *ydst = reinterpret_cast<char *>(y + (t0 - 1) * plane_elems + self * NC);               // layer t0
+    char *ydst = reinterpret_cast<char *>(y + (t0 - 1) * plane_elems + self * NC);               // layer t0, row 0
+    const size_t row_bytes = (size_t)nx * NC * sizeof(V);
     int issue_slot = 0;
     const char *issue_src = xsrc;
 
@@ -302,49 +366,65 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
         issue_src += plane_bytes;
         issue_slot = issue_slot + 1 == S::STAGES ? 0 : issue_slot + 1;
     };
-    // G_C' = G_C / 2 and G_M' = (h_t / 6) G_M of plane i held in ring slot si
-    auto plane_fields = [&](int i, int si, V *GC, V *GM) {
-        if (i >= i_lo && i <= i_hi && valid) {
-            const char *slot = ring + (size_t)si * slot_bytes;
-            auto get = [&](int r) {
-                const int dz = r / (3 * NY), dy = (r / 3) % NY, dx = r % 3;
-                return smem_node<NC, T>(slot, c0 + (dz * S::BY + dy) * S::BX + dx);
-            };
-            if (stdn) {
-                fields_std<D, NC, T, !NOV>(get, sc, (T)p.m, wxs, GC, GM);
+    // G_C' = G_C / 2 and G_M' = (h_t / 6) G_M of plane i (ring slot si) for the thread's RY outputs
+    auto plane_fields = [&](int i, int si, V (*GC)[NC], V (*GM)[NC]) {
+        const bool have = i >= i_lo && i <= i_hi;
+        const char *slot = ring + (size_t)si * slot_bytes;
+        if (have && RY > 1 && all_std) {
+            auto getq = [&](int q, int dx) { return smem_node<NC, T>(slot, c0 + q * S::BX + dx); };
+            fields_std_rows<NC, T, !NOV, RY>(getq, sc, (T)p.m, wxs, GC, GM);
+            return;
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            if (have && valid[r]) {
+                const int cr = c0 + r * S::BX;
+                auto get = [&](int q) {
+                    const int dz = q / (3 * NY), dy = (q / 3) % NY, dx = q % 3;
+                    return smem_node<NC, T>(slot, cr + (dz * S::BY + dy) * S::BX + dx);
+                };
+                if (stdn[r]) {
+                    fields_std<D, NC, T, !NOV>(get, sc, (T)p.m, wxs, GC[r], GM[r]);
+                } else {
+                    NodeCoef<D, T> kr;
+                    if (r == 0) kr = k;
+                    else node_coef<D, T>(p, ix, iy + r, iz, kr);
+                    if (NOV) fields_nov<D, NC, T>(get, kr, (T)p.m, GC[r], GM[r]);
+                    else fields<D, NC, T>(get, kr, GC[r], GM[r]);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) { GC[r][c] = cmul_r((T)0.5, GC[r][c]); GM[r][c] = cmul_r(h6, GM[r][c]); }
+                }
             } else {
-                if (NOV) fields_nov<D, NC, T>(get, k, (T)p.m, GC, GM);
-                else fields<D, NC, T>(get, k, GC, GM);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) { GC[c] = cmul_r((T)0.5, GC[c]); GM[c] = cmul_r(h6, GM[c]); }
+                for (int c = 0; c < NC; ++c) { GC[r][c] = cz<V>(); GM[r][c] = cz<V>(); }
             }
-        } else {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) { GC[c] = cz<V>(); GM[c] = cz<V>(); }
         }
     };
 
-    V accP[NC], accC[NC];
+    V accP[RY][NC], accC[RY][NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) { accP[c] = cz<V>(); accC[c] = cz<V>(); }
+    for (int r = 0; r < RY; ++r)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { accP[r][c] = cz<V>(); accC[r][c] = cz<V>(); }
     // y(pl-1) += G_C' + G_M'; y(pl) += (pl < N ? 4 G_M' : G_C' + 2 G_M'); y(pl+1) = G_M' - G_C'
-    auto accumulate = [&](int i, const V *GC, const V *GM) {
+    auto accumulate = [&](int i, V (*GC)[NC], V (*GM)[NC]) {
         const bool last = i >= i_last;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            accP[c] = cadd(accP[c], cadd(GC[c], GM[c]));
-            if (last) accC[c] = cadd(accC[c], cfma_r((T)2, GM[c], GC[c]));
-            else accC[c] = cfma_r((T)4, GM[c], accC[c]);
-        }
-        if (valid && i >= 2) {
-            store_node<NC, T>(reinterpret_cast<V *>(ydst), 0, accP);
-            ydst += plane_bytes;
-        }
+        for (int r = 0; r < RY; ++r) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            accP[c] = accC[c];
-            accC[c] = csub(GM[c], GC[c]);
+            for (int c = 0; c < NC; ++c) {
+                accP[r][c] = cadd(accP[r][c], cadd(GC[r][c], GM[r][c]));
+                if (last) accC[r][c] = cadd(accC[r][c], cfma_r((T)2, GM[r][c], GC[r][c]));
+                else accC[r][c] = cfma_r((T)4, GM[r][c], accC[r][c]);
+            }
+            if (valid[r] && i >= 2) store_node<NC, T>(reinterpret_cast<V *>(ydst + r * row_bytes), 0, accP[r]);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                accP[r][c] = accC[r][c];
+                accC[r][c] = csub(GM[r][c], GC[r][c]);
+            }
         }
+        if (i >= 2) ydst += plane_bytes;
     };
 
     if (S::PAIR) {
@@ -357,7 +437,7 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
             __syncthreads();
             issue_next(i + S::STAGES - 2);
             issue_next(i + S::STAGES - 1);
-            V GC0[NC], GM0[NC], GC1[NC], GM1[NC];
+            V GC0[RY][NC], GM0[RY][NC], GC1[RY][NC], GM1[RY][NC];
             plane_fields(i, si, GC0, GM0);
             plane_fields(i + 1, si + 1, GC1, GM1);
             si = (si + 2) & (S::STAGES - 1);
@@ -372,13 +452,14 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
             cp_async_wait<S::STAGES - 2>();
             __syncthreads();
             issue_next(i + S::STAGES - 1);
-            V GC[NC], GM[NC];
+            V GC[RY][NC], GM[RY][NC];
             plane_fields(i, si, GC, GM);
             si = si + 1 == S::STAGES ? 0 : si + 1;
             accumulate(i, GC, GM);
         }
     }
     cp_async_wait<0>();
+    (void)any_valid;
 }
 
 template <int D, int NC, typename T>
