@@ -42,6 +42,9 @@ SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_SM = 4.0     # 2 FP64 FMA per clock per SM (1/64 of the FP32 rate)
 FP32_FLOP_PER_CLK_SM = 256.0   # 128 FP32 FMA per clock per SM
 CLASSES = ("apply64", "apply32", "cast", "project", "update", "scale", "misc", "rhs")
+# DRAM read+write bytes per algorithmic byte of the df32 projection, from one ncu capture
+# (profiles/project_df_traffic_zb_2p1.md); valid for project_df_kernel as committed with it.
+PROJECT_DF_TRAFFIC_RATIO = 1.087
 
 
 def measured_peaks():
@@ -315,8 +318,19 @@ def main():
                 "avg_launch_us": 1e3 * d_ms / max(d_l, 1)}
     else:
         ach = d_b / (d_ms * 1e-3) / 1e9
+        traffic = None
+        launches_ran = d_l
+        if dom in ("project", "update"):
+            # per step one first-pass launch plus one gated second pass, which moves data
+            # only when it runs (reorths); achieved = bytes per launch / time per launch
+            launches_ran = sum(s["iters"] + s["reorths"] for s in stats)
+        if dom == "project" and PROJECT_DF_TRAFFIC_RATIO:
+            # average algorithmic bytes per launch that ran times the measured DRAM/algorithmic ratio
+            traffic = PROJECT_DF_TRAFFIC_RATIO * d_b / max(launches_ran, 1)
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_kind": hbm_kind, "avg_launch_us": 1e3 * d_ms / max(d_l, 1)}
+                "traffic": traffic, "traffic_unit": "bytes per launch", "peak_kind": hbm_kind,
+                "algorithmic_bytes_per_launch": d_b / max(launches_ran, 1),
+                "avg_launch_us": 1e3 * d_ms / max(launches_ran, 1)}
     kernels = {k: {"ms_share": (v[0] / kms if kms else None), "launches": int(v[1]),
                    "GBps": (v[2] / (v[0] * 1e-3) / 1e9 if v[0] else None),
                    "TFLOPps": (v[3] / (v[0] * 1e-3) / 1e12 if v[0] else None)} for k, v in tot.items() if v[1]}
