@@ -241,6 +241,20 @@ DST_API int dst_default_solve_opts(dst_solve_opts *opts);
 DST_API int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, dst_solve_stats *stats,
               void *stream);
 
+/*
+ * Observables of a solution, per unknown time layer t = 1..N_t, by trapezoidal
+ * sums over the spatial nodes (Sec. 4.2, Eq. 20; Sec. 4.3, Eq. 25; the charge
+ * monitored in Sec. 4.1): psi is a DEVICE FP64 solution (n_unknowns complex,
+ * the layout of dst_solve), out a DEVICE array of N_t x 5 doubles, row t-1 =
+ *   [ Q, Q_right, M_x, M_y, M_z ]
+ * with Q = sum_nodes w |psi|^2, Q_right the part at x > x0 (a node at x0
+ * counts one half), M_k = sum_nodes w x_k |psi|^2 (zero for axes the mesh does
+ * not have).  So <x_k>(t) = M_k / Q and the transmitted share T = Q_right / Q.
+ * Weights w: product over axes of h (periodic, Dirichlet interior nodes) or
+ * h with the two end nodes halved (open axes).  Deterministic (fixed order).
+ */
+DST_API int dst_observables(const dst_mesh *mesh, const void *psi, double x0, void *out, void *stream);
+
 /* Static, human-readable name of a status code. */
 DST_API const char *dst_status_string(int status);
 

@@ -25,7 +25,7 @@ EXPORTED = (
     "dst_create_mesh", "dst_destroy_mesh", "dst_mesh_sizes", "dst_set_mass", "dst_set_potential",
     "dst_set_initial_data", "dst_build_rhs", "dst_apply_operator", "dst_arnoldi_project",
     "dst_arnoldi_update", "dst_default_solve_opts", "dst_solve", "dst_status_string",
-    "dst_last_error_detail", "dst_arnoldi_project_noalloc",
+    "dst_last_error_detail", "dst_arnoldi_project_noalloc", "dst_observables",
 )
 
 
@@ -84,6 +84,7 @@ def _load():
         "dst_arnoldi_project": (c_int, [i64, c_int, vp, vp, vp, vp]),
         "dst_arnoldi_update": (c_int, [i64, c_int, vp, vp, vp, vp, vp]),
         "dst_arnoldi_project_noalloc": (c_int, [i64, c_int, vp, vp, vp, vp]),
+        "dst_observables": (c_int, [vp, vp, c_double, vp, vp]),
         "dst_default_solve_opts": (c_int, [P(dst_solve_opts)]),
         "dst_solve": (c_int, [vp, P(dst_solve_opts), vp, P(dst_solve_stats), vp]),
         "dst_status_string": (ctypes.c_char_p, [c_int]),
@@ -238,6 +239,16 @@ def dst_arnoldi_update(n, nvec, V, h, w, nrm2, stream=None):
     pn = _dev_ptr(nrm2, torch.float64, 1, "nrm2")
     return _check(_lib.dst_arnoldi_update(int(n), int(nvec), pV, ph, pw, pn, _stream(stream, V, w)),
                   "dst_arnoldi_update")
+
+
+def dst_observables(mesh, psi, x0, out, stream=None):
+    """Per-layer [Q, Q_right, M_x, M_y, M_z] of a solution (out: N_t x 5 float64 CUDA tensor)."""
+    import torch
+    ns, nu, nc = dst_mesh_sizes(mesh)
+    nt = nu // (ns * nc)
+    pp = _dev_ptr(psi, torch.complex128, nu, "psi")
+    po = _dev_ptr(out, torch.float64, 5 * nt, "out")
+    return _check(_lib.dst_observables(mesh, pp, float(x0), po, _stream(stream, psi, out)), "dst_observables")
 
 
 def dst_default_solve_opts():

@@ -27,6 +27,10 @@ def test_klein_3p1_full_size_matches_1p1_oracle():
         st = B.dst_solve(mesh.handle, {"restart": 30, "rtol": 1e-11, "max_iters": 20000, "mixed_precision": 1}, psi)
         torch.cuda.synchronize()
         assert st["status"] == 0, st
+        obs = torch.zeros((48, 5), dtype=torch.float64, device="cuda")
+        B.dst_observables(mesh.handle, psi, 0.0, obs)
+        torch.cuda.synchronize()
+        obs = obs.cpu().numpy()
         sol = psi.view(48, 48, 48, 47, 4).cpu().numpy()
     # 1+1 oracle on the x-t mesh: same x axis (Dirichlet, 48 elements on [-6, 6]), same t axis
     m1 = OM.Mesh(1, [48, 1, 1, 48], [-6.0, 0, 0, 0.0], [6.0, 1, 1, 3.0], [W.DIRICHLET, 0, 0])
@@ -45,3 +49,10 @@ def test_klein_3p1_full_size_matches_1p1_oracle():
         for iy in range(48):
             worst = max(worst, np.linalg.norm(sol[:, iz, iy] - ref) / nref)
     assert worst <= 1e-8, worst
+    # observables of a y, z-uniform solution are the 1+1 ones: transmitted share and <x>(t)
+    from oracle import observables as OB
+    ref_layers = ref[:, None, None, :, :]
+    T1 = np.array([OB.transmission(m1, ref_layers[n], 0.0)[0] for n in range(48)])
+    X1 = OB.mean_position(m1, ref_layers, 0)
+    assert np.allclose(obs[:, 1] / obs[:, 0], T1, rtol=0, atol=1e-8)
+    assert np.allclose(obs[:, 2] / obs[:, 0], X1, rtol=0, atol=1e-8)
