@@ -192,6 +192,9 @@ typedef struct {
                                (basis stored as FP32 hi/lo planes, 48-bit significand, error-free
                                FP32 products and sums, FP64 reductions; needs inner_cycles = 1),
                                1 = native FP64 (FP64 basis) */
+    int method;             /* Krylov method: 0 = restarted GMRES(restart) (default),
+                               1 = BiCGSTAB (van der Vorst 1992; FP64 only, mixed_precision
+                               must be 0; iters counts BiCGSTAB steps of two applies each) */
 } dst_solve_opts;
 
 /* Kernel classes of dst_solve_stats' per-class arrays. */
@@ -227,7 +230,7 @@ typedef struct {
 /* Fill opts with the defaults (restart 30, max_iters 100000, rtol 1e-8,
  * FP64, inner_rtol 1e-4, max_refine 100000, zero initial guess, no
  * profiling, one inner cycle per refinement, selective reorthogonalisation,
- * double-FP32 inner Gram-Schmidt). */
+ * double-FP32 inner Gram-Schmidt, GMRES). */
 DST_API int dst_default_solve_opts(dst_solve_opts *opts);
 
 /*

@@ -43,7 +43,7 @@ class dst_solve_opts(ctypes.Structure):
                 ("mixed_precision", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
                 ("profile", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("ortho", ctypes.c_int),
-                ("mixed_ortho", ctypes.c_int)]
+                ("mixed_ortho", ctypes.c_int), ("method", ctypes.c_int)]
 
 
 class dst_solve_stats(ctypes.Structure):

@@ -234,9 +234,94 @@ __global__ void axpy1_kernel(int64_t n, const double2 *__restrict__ d, double2 *
     }
 }
 
+// ---- BiCGSTAB (van der Vorst 1992) vector steps with device-resident scalars ----
+// sc (double2[8]): 0 rho, 1 alpha, 2 omega, 3 beta, 4 (rhat, v), 5 (t, s), 6 (t, t) in .x, 7 (rhat, r)
+
+__device__ __forceinline__ double2 cmulz(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cdivz(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// mode 0: beta = (rho_new / rho)(alpha / omega), rho = rho_new; 1: alpha = rho / (rhat, v);
+// 2: omega = (t, s) / (t, t); 3: initialise rho = alpha = omega = 1
+__global__ void bicg_scalar_kernel(int mode, double2 *sc) {
+    if (threadIdx.x != 0) return;
+    if (mode == 0) {
+        sc[3] = cmulz(cdivz(sc[7], sc[0]), cdivz(sc[1], sc[2]));
+        sc[0] = sc[7];
+    } else if (mode == 1) {
+        sc[1] = cdivz(sc[0], sc[4]);
+    } else if (mode == 2) {
+        sc[2] = make_double2(sc[5].x / sc[6].x, sc[5].y / sc[6].x);
+    } else {
+        sc[0] = sc[1] = sc[2] = make_double2(1.0, 0.0);
+    }
+}
+
+// p = r + beta (p - omega v)
+__global__ void bicg_p_kernel(int64_t n, const double2 *__restrict__ r, const double2 *__restrict__ v,
+                              double2 *__restrict__ p, const double2 *__restrict__ sc) {
+    const double2 beta = sc[3], omega = sc[2];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 ov = cmulz(omega, v[i]);
+        const double2 d = make_double2(p[i].x - ov.x, p[i].y - ov.y);
+        const double2 bd = cmulz(beta, d);
+        p[i] = make_double2(r[i].x + bd.x, r[i].y + bd.y);
+    }
+}
+
+// s = r - alpha v
+__global__ void bicg_s_kernel(int64_t n, const double2 *__restrict__ r, const double2 *__restrict__ v,
+                              double2 *__restrict__ s, const double2 *__restrict__ sc) {
+    const double2 alpha = sc[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 av = cmulz(alpha, v[i]);
+        s[i] = make_double2(r[i].x - av.x, r[i].y - av.y);
+    }
+}
+
+// x += alpha p + omega s; r = s - omega t; partials of ||r||^2 (CTA slices, fixed order)
+__global__ void __launch_bounds__(RED_THREADS)
+bicg_xr_kernel(int64_t n, double2 *__restrict__ x, const double2 *__restrict__ p, const double2 *__restrict__ s,
+               const double2 *__restrict__ t, double2 *__restrict__ r, const double2 *__restrict__ sc,
+               double *__restrict__ partials) {
+    __shared__ double sh[RED_THREADS / 32];
+    const double2 alpha = sc[1], omega = sc[2];
+    int64_t b, e;
+    slice(n, b, e);
+    double acc = 0.0;
+    for (int64_t i = b + threadIdx.x; i < e; i += RED_THREADS) {
+        const double2 ap = cmulz(alpha, p[i]), os = cmulz(omega, s[i]), ot = cmulz(omega, t[i]);
+        x[i] = make_double2(x[i].x + ap.x + os.x, x[i].y + ap.y + os.y);
+        const double2 rr = make_double2(s[i].x - ot.x, s[i].y - ot.y);
+        r[i] = rr;
+        acc = fma(rr.x, rr.x, fma(rr.y, rr.y, acc));
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
 }  // namespace dst
 
 using namespace dst;
+
+int dst_k_bicg_scalar(int mode, double2 *sc, cudaStream_t s) {
+    bicg_scalar_kernel<<<1, 32, 0, s>>>(mode, sc);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_bicg_p(int64_t n, const double2 *r, const double2 *v, double2 *p, const double2 *sc, cudaStream_t s);
+int dst_k_bicg_s(int64_t n, const double2 *r, const double2 *v, double2 *sv, const double2 *sc, cudaStream_t s);
+
+int dst_k_bicg_xr(int64_t n, double2 *x, const double2 *p, const double2 *sv, const double2 *t, double2 *r,
+                  const double2 *sc, double *nrm2, double *partials, int nblk, cudaStream_t s) {
+    bicg_xr_kernel<<<nblk, RED_THREADS, 0, s>>>(n, x, p, sv, t, r, sc, partials);
+    reduce_real_kernel<<<1, RED_THREADS, 0, s>>>(nblk, partials, nrm2, nullptr, nullptr);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
 
 static unsigned stream_blocks(int64_t n) {
     int64_t b = (n + 255) / 256;
@@ -305,6 +390,18 @@ int dst_k_cast_64_32(int64_t n, const double2 *src, float2 *dst, cudaStream_t s)
 
 int dst_k_cast_32_64(int64_t n, const float2 *src, double2 *dst, cudaStream_t s) {
     cast_32_64_kernel<<<stream_blocks(n), 256, 0, s>>>(n, src, dst);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_bicg_p(int64_t n, const double2 *r, const double2 *v, double2 *p, const double2 *sc, cudaStream_t s) {
+    bicg_p_kernel<<<stream_blocks(n), 256, 0, s>>>(n, r, v, p, sc);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_bicg_s(int64_t n, const double2 *r, const double2 *v, double2 *sv, const double2 *sc, cudaStream_t s) {
+    bicg_s_kernel<<<stream_blocks(n), 256, 0, s>>>(n, r, v, sv, sc);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }

@@ -39,3 +39,10 @@ int dst_k_update_df(int64_t n, int nvec, const float2 *V, const double2 *h, floa
 int dst_k_scale_df(int64_t n, float2 *v, const double *nrm2, cudaStream_t s);
 int dst_k_split_f64_df(int64_t n, const double2 *src, const double *nrm2, float2 *dst, cudaStream_t s);
 int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double2 *x, cudaStream_t s);
+
+// BiCGSTAB steps (blas.cu); sc = double2[8] device scalars (see blas.cu)
+int dst_k_bicg_scalar(int mode, double2 *sc, cudaStream_t s);
+int dst_k_bicg_p(int64_t n, const double2 *r, const double2 *v, double2 *p, const double2 *sc, cudaStream_t s);
+int dst_k_bicg_s(int64_t n, const double2 *r, const double2 *v, double2 *sv, const double2 *sc, cudaStream_t s);
+int dst_k_bicg_xr(int64_t n, double2 *x, const double2 *p, const double2 *sv, const double2 *t, double2 *r,
+                  const double2 *sc, double *nrm2, double *partials, int nblk, cudaStream_t s);

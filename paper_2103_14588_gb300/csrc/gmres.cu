@@ -389,6 +389,66 @@ struct Solver {
         return DST_OK;
     }
 
+    // BiCGSTAB (van der Vorst 1992) in FP64: two operator applies and four inner
+    // products per step; the scalars alpha, beta, omega stay on the device, so a
+    // step needs one host synchronisation (the residual norm for the stop test).
+    int bicgstab(double2 *x, const double2 *rhs, bool x_zero, double tol_abs, int max_iters, double &beta_out) {
+        const int64_t n = w.n;
+        const double dn = (double)n;
+        double2 *rhat = w.V, *r = w.V + n, *pv = w.V + 2 * n, *v = w.V + 3 * n, *sv = w.V + 4 * n, *t = w.V + 5 * n;
+        double2 *sc = w.h2;
+        auto dot = [&](const double2 *a, const double2 *bb, double2 *out) {
+            return run(K_PROJECT, 2, 32.0 * dn, 8.0 * dn,
+                       [&] { return dst_k_project(n, 1, a, bb, out, w.partials_c, nblk, s); });
+        };
+        double beta;
+        int rc = initial_residual(DST_FP64, x, rhs, x_zero, beta);       // V[0] = rhs - A x
+        if (rc) return rc;
+        if (!std::isfinite(beta)) return DST_ERR_NAN;
+        // The recursively updated residual drifts from rhs - A x; when it meets the
+        // tolerance but the true residual does not, the method restarts from x
+        // with the true residual as its new shadow vector.
+        while (beta > tol_abs && iters < max_iters) {
+            ++restarts;
+            DST_CUDA_TRY(cudaMemcpyAsync(r, rhat, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
+            DST_CUDA_TRY(cudaMemsetAsync(pv, 0, sizeof(double2) * n, s));
+            DST_CUDA_TRY(cudaMemsetAsync(v, 0, sizeof(double2) * n, s));
+            if ((rc = dst_k_bicg_scalar(3, sc, s))) return rc;
+            double rn = beta;
+            while (rn > tol_abs && iters < max_iters) {
+                if ((rc = dot(rhat, r, sc + 7))) return rc;                             // rho_new = (rhat, r)
+                if ((rc = dst_k_bicg_scalar(0, sc, s))) return rc;                      // beta, rho
+                if ((rc = run(K_MISC, 1, 64.0 * dn, 12.0 * dn, [&] { return dst_k_bicg_p(n, r, v, pv, sc, s); })))
+                    return rc;
+                if ((rc = apply(DST_FP64, pv, v))) return rc;                           // v = A p
+                if ((rc = dot(rhat, v, sc + 4))) return rc;
+                if ((rc = dst_k_bicg_scalar(1, sc, s))) return rc;                      // alpha
+                if ((rc = run(K_MISC, 1, 48.0 * dn, 8.0 * dn, [&] { return dst_k_bicg_s(n, r, v, sv, sc, s); })))
+                    return rc;
+                if ((rc = apply(DST_FP64, sv, t))) return rc;                           // t = A s
+                if ((rc = dot(t, sv, sc + 5))) return rc;
+                if ((rc = run(K_MISC, 2, 16.0 * dn, 4.0 * dn, [&] {
+                         return dst_k_nrm2(n, t, reinterpret_cast<double *>(sc + 6), w.partials_r, nblk, s);
+                     })))
+                    return rc;
+                if ((rc = dst_k_bicg_scalar(2, sc, s))) return rc;                      // omega
+                if ((rc = run(K_MISC, 2, 96.0 * dn, 24.0 * dn,
+                              [&] { return dst_k_bicg_xr(n, x, pv, sv, t, r, sc, w.nrm, w.partials_r, nblk, s); })))
+                    return rc;
+                DST_CUDA_TRY(cudaMemcpyAsync(w.host, w.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+                if ((rc = sync())) return rc;
+                ++iters;
+                rn = std::sqrt(w.host[0]);
+                resid_est = rn;
+                if (!std::isfinite(rn)) return DST_ERR_NAN;
+            }
+            if ((rc = initial_residual(DST_FP64, x, rhs, false, beta))) return rc;   // true residual
+            if (!std::isfinite(beta)) return DST_ERR_NAN;
+        }
+        beta_out = beta;
+        return DST_OK;
+    }
+
     // One GMRES(m) cycle for the correction equation A d = r (d = 0 on entry),
     // FP32 operator apply on a df32 basis with df32 Gram-Schmidt: V_0 = r/||r||
     // (||r||^2 in w.nrm[rslot]), d += V y at the end (FP64).
@@ -464,6 +524,7 @@ extern "C" int dst_default_solve_opts(dst_solve_opts *o) {
     o->profile = 0;
     o->ortho = 0;
     o->mixed_ortho = 0;
+    o->method = 0;
     return DST_OK;
 }
 
@@ -476,7 +537,7 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     sv.nblk = dst_reduction_blocks(mesh->n_unknowns);
     sv.nblk_proj = dst_projection_blocks(mesh->n_unknowns);
     sv.ortho = o.ortho;
-    int rc = setup_workspace(mesh, o.restart, mixed, sv.w);
+    int rc = setup_workspace(mesh, o.method == 1 ? std::max(o.restart, 5) : o.restart, mixed, sv.w);
     if (rc) return rc;
     static thread_local double *pinned = nullptr;
     if (!pinned) {
@@ -507,7 +568,10 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     }
     const double tol = o.rtol * bnorm;
     double beta = 0.0;
-    if (!mixed) {
+    if (o.method == 1) {
+        rc = sv.bicgstab(psi, sv.w.b, !o.use_initial_guess, tol, o.max_iters, beta);
+        if (rc) return rc;
+    } else if (!mixed) {
         rc = sv.gmres(DST_FP64, psi, sv.w.b, !o.use_initial_guess, tol, o.max_iters, beta);
         if (rc) return rc;
     } else {
@@ -580,7 +644,8 @@ extern "C" int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, 
     if (opts) o = *opts;
     if (!mesh || !psi || o.restart < 1 || o.restart > DST_MAX_VEC - 1 || o.max_iters < 0 || !(o.rtol >= 0) ||
         (o.mixed_precision && (!(o.inner_rtol > 0) || o.max_refine < 1)) || o.ortho < 0 || o.ortho > 1 ||
-        o.mixed_ortho < 0 || o.mixed_ortho > 1 || o.inner_cycles < 0) {
+        o.mixed_ortho < 0 || o.mixed_ortho > 1 || o.inner_cycles < 0 || o.method < 0 || o.method > 1 ||
+        (o.method == 1 && o.mixed_precision)) {
         rc = DST_ERR_ARG;
     } else if (!mesh->d_psi0) {
         rc = DST_ERR_STATE;

@@ -199,3 +199,31 @@ def test_zero_initial_data_gives_zero(torch, B):
     w.psi0 = np.zeros_like(w.psi0)
     x, st = _solve(torch, B, w)
     assert st["status"] == 0 and np.all(x == 0)
+
+
+@pytest.mark.parametrize("d,n_el,bc", [(1, [40, 1, 1, 25], [P]), (2, [12, 10, 1, 14], [P, P]),
+                                       (3, [5, 4, 4, 5], [P, D, D])])
+def test_bicgstab_matches_lu_and_oracle_iterates(torch, B, d, n_el, bc):
+    """BiCGSTAB (method 1).  On these non-normal systems the method is chaotic:
+    perturbing b by 1e-15 moves the oracle's own iterate by O(1) within 4-10
+    steps, but by at most 4e-12 after 2.  So the iterate after 2 steps is
+    compared with the oracle's BiCGSTAB, and the converged solution with LU."""
+    from oracle import solvers as OS
+    w = W.random_mesh(d, n_el, bc, seed=60 + d)
+    ref, A, b = _exact(w)
+    xo, _, _, _ = OS.bicgstab(lambda v: A @ v, b, rtol=1e-16, maxiter=2)
+    x2, st = _solve(torch, B, w, method=1, rtol=1e-16, max_iters=2)
+    assert st["status"] == 1 and st["iters"] == 2
+    assert rel_l2(x2, xo) <= 1e-9
+    x, st = _solve(torch, B, w, method=1, rtol=1e-13, max_iters=20000)
+    assert st["status"] == 0 and st["rel_resid_true"] <= 1e-13
+    assert rel_l2(x, ref) <= 1e-10
+
+
+def test_bicgstab_rejects_mixed(torch, B):
+    w = W.random_mesh(1, [8, 1, 1, 4], [P], seed=1)
+    with B.Mesh.from_workload(w) as mesh:
+        psi = torch.zeros(mesh.n_unknowns, dtype=torch.complex128, device="cuda")
+        with pytest.raises(B.DstError) as e:
+            B.dst_solve(mesh.handle, {"method": 1, "mixed_precision": 1}, psi)
+        assert e.value.code == B.DST_ERR_ARG

@@ -62,3 +62,12 @@ def test_givens_zeroes_second_entry():
         c, s = SO.givens(a, b)
         assert abs(-np.conj(s) * a + c * b) < 1e-15 * max(abs(a), abs(b), 1)
         assert abs(c * c + abs(s) ** 2 - 1) < 1e-15
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_bicgstab_equals_lu(d):
+    me, A, b = _system(d=d, nel=(10, 4, 3), nt=6)
+    x_lu = SO.dense_solve(A, b)
+    x, it, rel, ok = SO.bicgstab(lambda v: A @ v, b, rtol=1e-13, maxiter=20000)
+    assert ok and rel <= 1e-13 and it > 3
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) < 1e-10
