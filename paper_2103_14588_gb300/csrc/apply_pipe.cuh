@@ -43,7 +43,12 @@ struct PipeShape {
     // output per thread and an eight-plane ring fits comfortably; otherwise one
     // plane per step, 4 or 3 stages
     static constexpr bool PAIR = Tile::RY == 1 && BOX * NODE_BYTES * 8 <= 72 * 1024;
-    static constexpr int STAGES = PAIR ? 8 : ((BOX * NODE_BYTES * 4 <= 96 * 1024) ? 4 : 3);
+    // the whole chunk (TT planes + two halo planes) resident at once when it is
+    // small: every copy is issued before the first plane is consumed, so the
+    // latency of the HBM reads is paid once per CTA instead of once per slot
+    static constexpr bool FULL = !PAIR && (Tile::TT + 2) * BOX * NODE_BYTES <= 56 * 1024;
+    static constexpr int STAGES =
+        FULL ? Tile::TT + 2 : (PAIR ? 8 : ((BOX * NODE_BYTES * 4 <= 96 * 1024) ? 4 : 3));
     static constexpr int SMEM = STAGES * BOX * NODE_BYTES;
 };
 
@@ -55,6 +60,19 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool ok
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// wait_group with a count known only after unrolling (0 .. 15)
+__device__ __forceinline__ void cp_async_wait_n(int n) {
+    switch (n) {
+    case 0: cp_async_wait<0>(); break;   case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;   case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;   case 5: cp_async_wait<5>(); break;
+    case 6: cp_async_wait<6>(); break;   case 7: cp_async_wait<7>(); break;
+    case 8: cp_async_wait<8>(); break;   case 9: cp_async_wait<9>(); break;
+    case 10: cp_async_wait<10>(); break; case 11: cp_async_wait<11>(); break;
+    case 12: cp_async_wait<12>(); break; case 13: cp_async_wait<13>(); break;
+    case 14: cp_async_wait<14>(); break; default: cp_async_wait<15>(); break;
+    }
+}
 
 // The 16-byte copies one thread issues for every plane: source byte offset
 // within a time layer (-1: outside a non-periodic boundary, zero-filled) and
@@ -281,8 +299,11 @@ __device__ __forceinline__ void fields_std_rows(Get get, const StdConst<T> &sc, 
     }
 }
 
-template <int D, int NC, typename T, bool NOV>
-__global__ void __launch_bounds__(PipeShape<D, NC, T>::NTHR, (D == 3 || sizeof(T) == 8) ? 1 : 3)
+// STD: every node of the mesh has the standard interior stencils on every axis
+// (no open axis), so the general-coefficient branch is not compiled in.
+template <int D, int NC, typename T, bool NOV, bool STD>
+__global__ void __launch_bounds__(PipeShape<D, NC, T>::NTHR,
+                                  sizeof(T) == 8 ? 1 : (D == 3 ? (STD ? 2 : 1) : 3))
 apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typename C2<T>::type *__restrict__ y,
                   int64_t tiles_x, int64_t tiles_y) {
     using V = typename C2<T>::type;
@@ -370,6 +391,26 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
     auto plane_fields = [&](int i, int si, V (*GC)[NC], V (*GM)[NC]) {
         const bool have = i >= i_lo && i <= i_hi;
         const char *slot = ring + (size_t)si * slot_bytes;
+        if (STD) {
+            // rows / columns past the mesh end read initialised shared memory
+            // (wrapped or zero-filled halo) and are not stored
+            if (!have) {
+#pragma unroll
+                for (int r = 0; r < RY; ++r)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) { GC[r][c] = cz<V>(); GM[r][c] = cz<V>(); }
+            } else if (RY > 1) {
+                auto getq = [&](int q, int dx) { return smem_node<NC, T>(slot, c0 + q * S::BX + dx); };
+                fields_std_rows<NC, T, !NOV, RY>(getq, sc, (T)p.m, wxs, GC, GM);
+            } else {
+                auto get = [&](int q) {
+                    const int dz = q / (3 * NY), dy = (q / 3) % NY, dx = q % 3;
+                    return smem_node<NC, T>(slot, c0 + (dz * S::BY + dy) * S::BX + dx);
+                };
+                fields_std<D, NC, T, !NOV>(get, sc, (T)p.m, wxs, GC[0], GM[0]);
+            }
+            return;
+        }
         if (have && RY > 1 && all_std) {
             auto getq = [&](int q, int dx) { return smem_node<NC, T>(slot, c0 + q * S::BX + dx); };
             fields_std_rows<NC, T, !NOV, RY>(getq, sc, (T)p.m, wxs, GC, GM);
@@ -427,7 +468,21 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
         if (i >= 2) ydst += plane_bytes;
     };
 
-    if (S::PAIR) {
+    if (S::FULL) {
+        // every plane of the chunk in flight before the first is consumed
+#pragma unroll
+        for (int i = 0; i < S::STAGES; ++i) issue_next(i);
+#pragma unroll
+        for (int i = 0; i < S::STAGES; ++i) {
+            if (i < nplanes) {
+                cp_async_wait_n(S::STAGES - 1 - i);
+                __syncthreads();
+                V GC[RY][NC], GM[RY][NC];
+                plane_fields(i, i, GC, GM);
+                accumulate(i, GC, GM);
+            }
+        }
+    } else if (S::PAIR) {
         // ring of 8: planes i, i+1 computed while up to six more are in flight
 #pragma unroll
         for (int i = 0; i < S::STAGES - 2; ++i) issue_next(i);
@@ -476,14 +531,20 @@ int launch_apply_pipe(const OpParams &p, const typename C2<T>::type *x, typename
     if (p.ax[0].n * p.ax[1].n * p.ax[2].n * S::NODE_BYTES >= (1LL << 31)) return launch_apply<D, NC, T>(p, x, y, s);
     dim3 grid((unsigned)tiles, (unsigned)chunks);
     // the shared-memory opt-in is a per-device function attribute: set it once per device
-    static bool configured[2][DST_MAX_DEVICES_APPLY] = {};
+    static bool configured[4][DST_MAX_DEVICES_APPLY] = {};
     int dev = 0;
     DST_CUDA_TRY(cudaGetDevice(&dev));
     const int nov = p.vmode == 2 ? 1 : 0;
-    auto kern = nov ? apply_pipe_kernel<D, NC, T, true> : apply_pipe_kernel<D, NC, T, false>;
-    if (dev < 0 || dev >= DST_MAX_DEVICES_APPLY || !configured[nov][dev]) {
+    bool all_std = true;        // no open axis: every node has the standard stencils
+    for (int k = 0; k < D; ++k) all_std = all_std && p.ax[k].bc != DST_BC_OPEN;
+    const int var = nov + 2 * (all_std ? 1 : 0);
+    auto kern = var == 0   ? apply_pipe_kernel<D, NC, T, false, false>
+                : var == 1 ? apply_pipe_kernel<D, NC, T, true, false>
+                : var == 2 ? apply_pipe_kernel<D, NC, T, false, true>
+                           : apply_pipe_kernel<D, NC, T, true, true>;
+    if (dev < 0 || dev >= DST_MAX_DEVICES_APPLY || !configured[var][dev]) {
         DST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
-        if (dev >= 0 && dev < DST_MAX_DEVICES_APPLY) configured[nov][dev] = true;
+        if (dev >= 0 && dev < DST_MAX_DEVICES_APPLY) configured[var][dev] = true;
     }
     kern<<<grid, S::NTHR, S::SMEM, s>>>(p, x, y, tx, ty);
     DST_CUDA_TRY(cudaGetLastError());
