@@ -191,7 +191,11 @@ typedef struct {
     int mixed_ortho;        /* mixed only: arithmetic of the inner Gram-Schmidt.  0 = double-FP32
                                (basis stored as FP32 hi/lo planes, 48-bit significand, error-free
                                FP32 products and sums, FP64 reductions; needs inner_cycles = 1),
-                               1 = native FP64 (FP64 basis) */
+                               1 = native FP64 (FP64 basis),
+                               2 = FP32-stored basis (8 B per entry, half the traffic of 0) with
+                               the same error-free products and compensated sums: inner products
+                               and updates are FP64-class on the stored values, each new basis
+                               vector is rounded to FP32 once (needs inner_cycles = 1) */
     int method;             /* Krylov method: 0 = restarted GMRES(restart) (default),
                                1 = BiCGSTAB (van der Vorst 1992; FP64 only, mixed_precision
                                must be 0; iters counts BiCGSTAB steps of two applies each) */

@@ -30,15 +30,19 @@ int dst_k_reduce_real(int nblk, const double *partials, double *out, cudaStream_
 // entries is float2 hi[n] followed by float2 lo[n].  The projection and the
 // update reduce across CTAs inside the kernel (last CTA to take a ticket);
 // ticket points to a zero-initialised counter that the kernel leaves at zero.
+// vlo = false: every vector (basis and w) is the hi plane alone, n float2,
+// and w_hi_only must be true.
 int dst_k_project_df(int64_t n, int nvec, const float2 *V, const float2 *w, bool w_hi_only, double2 *h,
                      double2 *partials, int nblk, cudaStream_t s, double *wnrm2, double *wnrm_partials,
-                     const double *gate, unsigned *ticket);
+                     const double *gate, unsigned *ticket, bool vlo = true);
 int dst_k_update_df(int64_t n, int nvec, const float2 *V, const double2 *h, float2 *w, bool w_hi_only, double *nrm2,
                     double *partials, int nblk, cudaStream_t s, const double *gate, double *counter,
-                    unsigned *ticket);
-int dst_k_scale_df(int64_t n, float2 *v, const double *nrm2, cudaStream_t s);
-int dst_k_split_f64_df(int64_t n, const double2 *src, const double *nrm2, float2 *dst, cudaStream_t s);
-int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double2 *x, cudaStream_t s);
+                    unsigned *ticket, bool vlo = true);
+int dst_k_scale_df(int64_t n, float2 *v, const double *nrm2, cudaStream_t s, bool vlo = true);
+int dst_k_split_f64_df(int64_t n, const double2 *src, const double *nrm2, float2 *dst, cudaStream_t s,
+                       bool vlo = true);
+int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double2 *x, cudaStream_t s,
+                     bool vlo = true);
 
 // BiCGSTAB steps (blas.cu); sc = double2[8] device scalars (see blas.cu)
 int dst_k_bicg_scalar(int mode, double2 *sc, cudaStream_t s);

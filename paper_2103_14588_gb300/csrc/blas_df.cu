@@ -19,6 +19,12 @@
 // Layout of a df32 complex vector of n entries: float2 hi[n] followed by
 // float2 lo[n] (re, im interleaved in each plane).  The hi plane alone is the
 // vector rounded to FP32 - the input the FP32 operator apply reads directly.
+//
+// Kernels templated on VL = false work on a basis stored as the hi plane
+// alone (8 bytes per complex entry, half the traffic): the stored vectors are
+// FP32 numbers, but the products are still exact (TwoProd) and the sums
+// compensated, so inner products and updates keep FP64-class accuracy with
+// respect to the stored values; updated vectors are rounded to FP32 once.
 #include "blas.h"
 
 namespace dst {
@@ -91,17 +97,27 @@ __device__ __forceinline__ void df_slice2(int64_t n, int64_t &b, int64_t &e) {
     e = b + per < n ? b + per : n;
 }
 
-// acc += conj(v) w for one complex entry, df32 (v = vh + vl, w = ah + al)
-template <bool W_HI_ONLY>
+// (p, e): p + e = a b exactly, plus the lo cross terms that are present
+template <bool AL, bool BL>
+__device__ __forceinline__ void df_prod_t(float ah, float al, float bh, float bl, float &p, float &e) {
+    p = ah * bh;
+    e = fmaf(ah, bh, -p);
+    if (BL) e = fmaf(ah, bl, e);
+    if (AL) e = fmaf(al, bh, e);
+}
+
+// acc += conj(v) w for one complex entry, df32 (v = vh + vl, w = ah + al);
+// VL / WL: whether v / w carry a lo plane
+template <bool VL, bool WL>
 __device__ __forceinline__ void cdot_acc(float vhr, float vhi, float vlr, float vli, float ar, float ai, float alr,
                                          float ali, DfAcc &re, DfAcc &im) {
     float p1, e1, p2, e2;
-    df_prod(vhr, vlr, ar, W_HI_ONLY ? 0.f : alr, p1, e1);
-    df_prod(vhi, vli, ai, W_HI_ONLY ? 0.f : ali, p2, e2);
+    df_prod_t<VL, WL>(vhr, vlr, ar, alr, p1, e1);
+    df_prod_t<VL, WL>(vhi, vli, ai, ali, p2, e2);
     re.add(p1, e1);
     re.add(p2, e2);
-    df_prod(vhr, vlr, ai, W_HI_ONLY ? 0.f : ali, p1, e1);
-    df_prod(vhi, vli, ar, W_HI_ONLY ? 0.f : alr, p2, e2);
+    df_prod_t<VL, WL>(vhr, vlr, ai, ali, p1, e1);
+    df_prod_t<VL, WL>(vhi, vli, ar, alr, p2, e2);
     im.add(p1, e1);
     im.add(-p2, -e2);
 }
@@ -112,7 +128,7 @@ __device__ __forceinline__ void cdot_acc(float vhr, float vhi, float vlr, float 
 // planes) and DF_GROUP basis vectors per sweep over its slice.
 // The last CTA to finish (atomic ticket) sums every CTA's partials in CTA
 // order and writes h (and ||w||^2): a deterministic single-kernel reduction.
-template <bool W_HI_ONLY>
+template <bool W_HI_ONLY, bool VL>
 __global__ void __launch_bounds__(DF_THREADS)
 project_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float2 *__restrict__ w,
                   double2 *__restrict__ partials, double *__restrict__ wnrm_partials, const double *gate,
@@ -142,24 +158,25 @@ project_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float
             float4 vh[DF_GROUP], vl[DF_GROUP];
 #pragma unroll
             for (int g = 0; g < DF_GROUP; ++g) {
+                vl[g] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (g < gv) {
-                    const float4 *vj = reinterpret_cast<const float4 *>(V + (int64_t)(j0 + g) * 2 * n);
+                    const float4 *vj = reinterpret_cast<const float4 *>(V + (int64_t)(j0 + g) * (VL ? 2 : 1) * n);
                     vh[g] = vj[q];
-                    vl[g] = vj[(n >> 1) + q];
+                    if (VL) vl[g] = vj[(n >> 1) + q];
                 }
             }
             if (j0 == 0) {
                 float p, r;
-                df_prod(a.x, al.x, a.x, al.x, p, r); wn.add(p, r);
-                df_prod(a.y, al.y, a.y, al.y, p, r); wn.add(p, r);
-                df_prod(a.z, al.z, a.z, al.z, p, r); wn.add(p, r);
-                df_prod(a.w, al.w, a.w, al.w, p, r); wn.add(p, r);
+                df_prod_t<!W_HI_ONLY, !W_HI_ONLY>(a.x, al.x, a.x, al.x, p, r); wn.add(p, r);
+                df_prod_t<!W_HI_ONLY, !W_HI_ONLY>(a.y, al.y, a.y, al.y, p, r); wn.add(p, r);
+                df_prod_t<!W_HI_ONLY, !W_HI_ONLY>(a.z, al.z, a.z, al.z, p, r); wn.add(p, r);
+                df_prod_t<!W_HI_ONLY, !W_HI_ONLY>(a.w, al.w, a.w, al.w, p, r); wn.add(p, r);
             }
 #pragma unroll
             for (int g = 0; g < DF_GROUP; ++g) {
                 if (g < gv) {
-                    cdot_acc<W_HI_ONLY>(vh[g].x, vh[g].y, vl[g].x, vl[g].y, a.x, a.y, al.x, al.y, re[g], im[g]);
-                    cdot_acc<W_HI_ONLY>(vh[g].z, vh[g].w, vl[g].z, vl[g].w, a.z, a.w, al.z, al.w, re[g], im[g]);
+                    cdot_acc<VL, !W_HI_ONLY>(vh[g].x, vh[g].y, vl[g].x, vl[g].y, a.x, a.y, al.x, al.y, re[g], im[g]);
+                    cdot_acc<VL, !W_HI_ONLY>(vh[g].z, vh[g].w, vl[g].z, vl[g].w, a.z, a.w, al.z, al.w, re[g], im[g]);
                 }
             }
         }
@@ -214,15 +231,16 @@ project_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float
 }
 
 // acc -= v c for one complex entry (v df32, c = (re_hi, re_lo, im_hi, im_lo))
+template <bool VL = true>
 __device__ __forceinline__ void caxpy_sub(float vhr, float vhi, float vlr, float vli, const float4 &c, DfAcc &ar,
                                           DfAcc &ai) {
     float p1, e1, p2, e2;
-    df_prod(vhr, vlr, c.x, c.y, p1, e1);     // vr hr
-    df_prod(vhi, vli, c.z, c.w, p2, e2);     // vi hi
+    df_prod_t<VL, true>(vhr, vlr, c.x, c.y, p1, e1);     // vr hr
+    df_prod_t<VL, true>(vhi, vli, c.z, c.w, p2, e2);     // vi hi
     ar.add(-p1, -e1);
     ar.add(p2, e2);
-    df_prod(vhr, vlr, c.z, c.w, p1, e1);     // vr hi
-    df_prod(vhi, vli, c.x, c.y, p2, e2);     // vi hr
+    df_prod_t<VL, true>(vhr, vlr, c.z, c.w, p1, e1);     // vr hi
+    df_prod_t<VL, true>(vhi, vli, c.x, c.y, p2, e2);     // vi hr
     ai.add(-p1, -e1);
     ai.add(-p2, -e2);
 }
@@ -236,7 +254,7 @@ __device__ __forceinline__ void renorm(DfAcc &a) {
 // w <- w - sum_j V_j h_j in df32 (h given in FP64, split per CTA), and
 // partials of ||w||^2 after the update.  W_HI_ONLY: w's lo plane is read as
 // zero.  Two neighbouring entries per thread step, as in the projection.
-template <bool W_HI_ONLY>
+template <bool W_HI_ONLY, bool VL>
 __global__ void __launch_bounds__(DF_THREADS)
 update_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double2 *__restrict__ h,
                  float2 *__restrict__ w, double *__restrict__ nrm_partials, const double *gate,
@@ -265,28 +283,36 @@ update_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double
         ar1.hi = a.z; ar1.lo = al.z; ai1.hi = a.w; ai1.lo = al.w;
         // software pipelining: the planes of V_{j+1} are loaded before V_j is combined
         const float4 *v0 = reinterpret_cast<const float4 *>(V);
-        float4 vh = v0[q], vl = v0[(n >> 1) + q];
+        const int64_t vstride = (VL ? 2 : 1) * n;
+        float4 vh = v0[q], vl = VL ? v0[(n >> 1) + q] : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int j = 0; j < nvec; ++j) {
             float4 nh = vh, nl = vl;
             if (j + 1 < nvec) {
-                const float4 *vn = reinterpret_cast<const float4 *>(V + (int64_t)(j + 1) * 2 * n);
+                const float4 *vn = reinterpret_cast<const float4 *>(V + (int64_t)(j + 1) * vstride);
                 nh = vn[q];
-                nl = vn[(n >> 1) + q];
+                if (VL) nl = vn[(n >> 1) + q];
             }
             const float4 c = hs[j];
-            caxpy_sub(vh.x, vh.y, vl.x, vl.y, c, ar0, ai0);
-            caxpy_sub(vh.z, vh.w, vl.z, vl.w, c, ar1, ai1);
+            caxpy_sub<VL>(vh.x, vh.y, vl.x, vl.y, c, ar0, ai0);
+            caxpy_sub<VL>(vh.z, vh.w, vl.z, vl.w, c, ar1, ai1);
             vh = nh;
             vl = nl;
         }
         renorm(ar0); renorm(ai0); renorm(ar1); renorm(ai1);
         wh[q] = make_float4(ar0.hi, ai0.hi, ar1.hi, ai1.hi);
-        wl[q] = make_float4(ar0.lo, ai0.lo, ar1.lo, ai1.lo);
         float p, r;
-        df_prod(ar0.hi, ar0.lo, ar0.hi, ar0.lo, p, r); nr.add(p, r);
-        df_prod(ai0.hi, ai0.lo, ai0.hi, ai0.lo, p, r); nr.add(p, r);
-        df_prod(ar1.hi, ar1.lo, ar1.hi, ar1.lo, p, r); nr.add(p, r);
-        df_prod(ai1.hi, ai1.lo, ai1.hi, ai1.lo, p, r); nr.add(p, r);
+        if (VL) {
+            wl[q] = make_float4(ar0.lo, ai0.lo, ar1.lo, ai1.lo);
+            df_prod(ar0.hi, ar0.lo, ar0.hi, ar0.lo, p, r); nr.add(p, r);
+            df_prod(ai0.hi, ai0.lo, ai0.hi, ai0.lo, p, r); nr.add(p, r);
+            df_prod(ar1.hi, ar1.lo, ar1.hi, ar1.lo, p, r); nr.add(p, r);
+            df_prod(ai1.hi, ai1.lo, ai1.hi, ai1.lo, p, r); nr.add(p, r);
+        } else {        // the norm of the stored (rounded) vector
+            df_prod_t<false, false>(ar0.hi, 0.f, ar0.hi, 0.f, p, r); nr.add(p, r);
+            df_prod_t<false, false>(ai0.hi, 0.f, ai0.hi, 0.f, p, r); nr.add(p, r);
+            df_prod_t<false, false>(ar1.hi, 0.f, ar1.hi, 0.f, p, r); nr.add(p, r);
+            df_prod_t<false, false>(ai1.hi, 0.f, ai1.hi, 0.f, p, r); nr.add(p, r);
+        }
     }
     const double s_ = dfwarp_sum(nr);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s_;
@@ -316,7 +342,9 @@ update_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double
     }
 }
 
-// v <- v / sqrt(*nrm2) in df32 (both planes).
+// v <- v / sqrt(*nrm2) in df32 (both planes; VL = false: the hi plane,
+// rounded once to FP32).
+template <bool VL>
 __global__ void scale_df_kernel(int64_t n, float2 *__restrict__ v, const double *__restrict__ nrm2) {
     __shared__ float s_sh[2];     // split of 1/sqrt, once per CTA (FP64 division is slow here)
     if (threadIdx.x == 0) {
@@ -328,7 +356,7 @@ __global__ void scale_df_kernel(int64_t n, float2 *__restrict__ v, const double 
     const float sh = s_sh[0], sl = s_sh[1];
     float2 *vh = v, *vl = v + n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 a = vh[i], al = vl[i];
+        const float2 a = vh[i], al = VL ? vl[i] : make_float2(0.f, 0.f);
         float p, e, s, t;
         df_prod(a.x, al.x, sh, sl, p, e);
         s = p + e; t = e - (s - p);
@@ -338,11 +366,13 @@ __global__ void scale_df_kernel(int64_t n, float2 *__restrict__ v, const double 
         s = p + e; t = e - (s - p);
         oh.y = s; ol.y = t;
         vh[i] = oh;
-        vl[i] = ol;
+        if (VL) vl[i] = ol;
     }
 }
 
-// dst (df32) <- src (FP64) / sqrt(*nrm2): the restart vector of a cycle.
+// dst (df32) <- src (FP64) / sqrt(*nrm2): the restart vector of a cycle
+// (VL = false: rounded to FP32).
+template <bool VL>
 __global__ void split_f64_df_kernel(int64_t n, const double2 *__restrict__ src, const double *__restrict__ nrm2,
                                     float2 *__restrict__ dst) {
     __shared__ double s_sh;
@@ -355,12 +385,13 @@ __global__ void split_f64_df_kernel(int64_t n, const double2 *__restrict__ src, 
         const double xr = a.x * sc, xi = a.y * sc;
         const float hr = (float)xr, hi = (float)xi;
         dh[i] = make_float2(hr, hi);
-        dl[i] = make_float2((float)(xr - (double)hr), (float)(xi - (double)hi));
+        if (VL) dl[i] = make_float2((float)(xr - (double)hr), (float)(xi - (double)hi));
     }
 }
 
 // x (FP64) <- x + sum_j V_j y_j with V in df32 and y in FP64 (end of a
 // cycle): the sum runs in df32 (y split once per CTA), one conversion per entry.
+template <bool VL>
 __global__ void __launch_bounds__(DF_THREADS)
 combine_df_kernel(int64_t n, int k, const float2 *__restrict__ V, const double2 *__restrict__ y,
                   double2 *__restrict__ x) {
@@ -376,9 +407,9 @@ combine_df_kernel(int64_t n, int k, const float2 *__restrict__ V, const double2 
         ar.zero();
         ai.zero();
         for (int j = 0; j < k; ++j) {
-            const float2 *vj = V + (int64_t)j * 2 * n;
-            const float2 vh = vj[i], vl = vj[n + i];
-            caxpy_sub(vh.x, vh.y, vl.x, vl.y, ys[j], ar, ai);     // acc -= v (-y) = acc + v y
+            const float2 *vj = V + (int64_t)j * (VL ? 2 : 1) * n;
+            const float2 vh = vj[i], vl = VL ? vj[n + i] : make_float2(0.f, 0.f);
+            caxpy_sub<VL>(vh.x, vh.y, vl.x, vl.y, ys[j], ar, ai);     // acc -= v (-y) = acc + v y
         }
         double2 acc = x[i];
         acc.x += ar.value();
@@ -399,46 +430,53 @@ static unsigned df_stream_blocks(int64_t n) {
 
 int dst_k_project_df(int64_t n, int nvec, const float2 *V, const float2 *w, bool w_hi_only, double2 *h,
                      double2 *partials, int nblk, cudaStream_t s, double *wnrm2, double *wnrm_partials,
-                     const double *gate, unsigned *ticket) {
+                     const double *gate, unsigned *ticket, bool vlo) {
     if (n & 1) return DST_ERR_ARG;     // two entries per 16-byte load
-    if (w_hi_only)
-        project_df_kernel<true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wnrm2 ? wnrm_partials : nullptr,
-                                                            gate, h, wnrm2, ticket);
+    if (!vlo && !w_hi_only) return DST_ERR_ARG;     // an FP32-stored basis has no lo planes at all
+    double *wp = wnrm2 ? wnrm_partials : nullptr;
+    if (!vlo)
+        project_df_kernel<true, false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wp, gate, h, wnrm2, ticket);
+    else if (w_hi_only)
+        project_df_kernel<true, true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wp, gate, h, wnrm2, ticket);
     else
-        project_df_kernel<false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wnrm2 ? wnrm_partials : nullptr,
-                                                             gate, h, wnrm2, ticket);
+        project_df_kernel<false, true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wp, gate, h, wnrm2, ticket);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
 
 int dst_k_update_df(int64_t n, int nvec, const float2 *V, const double2 *h, float2 *w, bool w_hi_only, double *nrm2,
                     double *partials, int nblk, cudaStream_t s, const double *gate, double *counter,
-                    unsigned *ticket) {
+                    unsigned *ticket, bool vlo) {
     if (n & 1) return DST_ERR_ARG;
-    if (w_hi_only)
-        update_df_kernel<true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, nrm2 ? partials : nullptr, gate, nrm2,
-                                                           counter, ticket);
+    if (!vlo && !w_hi_only) return DST_ERR_ARG;
+    double *pp = nrm2 ? partials : nullptr;
+    if (!vlo)
+        update_df_kernel<true, false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, pp, gate, nrm2, counter, ticket);
+    else if (w_hi_only)
+        update_df_kernel<true, true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, pp, gate, nrm2, counter, ticket);
     else
-        update_df_kernel<false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, nrm2 ? partials : nullptr, gate, nrm2,
-                                                            counter, ticket);
+        update_df_kernel<false, true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, pp, gate, nrm2, counter, ticket);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
 
-int dst_k_scale_df(int64_t n, float2 *v, const double *nrm2, cudaStream_t s) {
-    scale_df_kernel<<<df_stream_blocks(n), 256, 0, s>>>(n, v, nrm2);
+int dst_k_scale_df(int64_t n, float2 *v, const double *nrm2, cudaStream_t s, bool vlo) {
+    if (vlo) scale_df_kernel<true><<<df_stream_blocks(n), 256, 0, s>>>(n, v, nrm2);
+    else scale_df_kernel<false><<<df_stream_blocks(n), 256, 0, s>>>(n, v, nrm2);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
 
-int dst_k_split_f64_df(int64_t n, const double2 *src, const double *nrm2, float2 *dst, cudaStream_t s) {
-    split_f64_df_kernel<<<df_stream_blocks(n), 256, 0, s>>>(n, src, nrm2, dst);
+int dst_k_split_f64_df(int64_t n, const double2 *src, const double *nrm2, float2 *dst, cudaStream_t s, bool vlo) {
+    if (vlo) split_f64_df_kernel<true><<<df_stream_blocks(n), 256, 0, s>>>(n, src, nrm2, dst);
+    else split_f64_df_kernel<false><<<df_stream_blocks(n), 256, 0, s>>>(n, src, nrm2, dst);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
 
-int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double2 *x, cudaStream_t s) {
-    combine_df_kernel<<<df_stream_blocks(n), DF_THREADS, 0, s>>>(n, k, V, y, x);
+int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double2 *x, cudaStream_t s, bool vlo) {
+    if (vlo) combine_df_kernel<true><<<df_stream_blocks(n), DF_THREADS, 0, s>>>(n, k, V, y, x);
+    else combine_df_kernel<false><<<df_stream_blocks(n), DF_THREADS, 0, s>>>(n, k, V, y, x);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }

@@ -246,10 +246,11 @@ struct Solver {
                                              second ? w.nrm + 6 : nullptr); });
     }
     // account a gated second pass over nv basis vectors that did run
-    void count_second_pass(int nv, bool df) {
+    // bytes of a second Gram-Schmidt pass that ran (vb: bytes per stored entry)
+    void count_second_pass(int nv, double vb = 16.0) {
         const double n = (double)w.n;
-        const double pb = df ? 16.0 * n * (nv + 1) : 16.0 * n * (nv + 1);
-        const double ub = 16.0 * n * (nv + 2);
+        const double pb = vb * n * (nv + 1);
+        const double ub = vb * n * (nv + 2);
         prof.bytes[K_PROJECT] += pb; prof.flops[K_PROJECT] += 8.0 * n * nv;
         prof.bytes[K_UPDATE] += ub; prof.flops[K_UPDATE] += 8.0 * n * nv;
         bytes += pb + ub;
@@ -367,7 +368,7 @@ struct Solver {
                 if ((rc = update(nv, w.h2, wv, w.nrm, gate, true))) return rc;
                 if ((rc = scale(wv))) return rc;     // normalise on the device (1/sqrt(nrm))
                 if ((rc = read_step(nv))) return rc;
-                if (second_pass_ran() && gate) count_second_pass(nv, false);
+                if (second_pass_ran() && gate) count_second_pass(nv);
                 ++iters;
                 if ((rc = take_column(hs, j, breakdown))) return rc;
                 k = j + 1;
@@ -452,48 +453,53 @@ struct Solver {
     // One GMRES(m) cycle for the correction equation A d = r (d = 0 on entry),
     // FP32 operator apply on a df32 basis with df32 Gram-Schmidt: V_0 = r/||r||
     // (||r||^2 in w.nrm[rslot]), d += V y at the end (FP64).
-    int cycle_df(double2 *d, const double2 *r, int rslot, double rnorm, double tol_abs, int max_iters) {
+    // vlo = false: the basis is stored in FP32 (hi planes only, 8 B per entry)
+    // and the same compensated kernels run on it.
+    int cycle_df(double2 *d, const double2 *r, int rslot, double rnorm, double tol_abs, int max_iters, bool vlo) {
         const int m = w.m;
         const int64_t n = w.n;
         const double dn = (double)n;
-        float2 *Vd = reinterpret_cast<float2 *>(w.V);   // (m+1) df32 vectors, 2n float2 each
-        int rc = run(K_SCALE, 1, 32.0 * dn, 2.0 * dn,
-                     [&] { return dst_k_split_f64_df(n, r, w.nrm + rslot, Vd, s); });
+        const double vb = vlo ? 16.0 : 8.0;             // bytes per stored basis entry
+        const int64_t vs = (vlo ? 2 : 1) * n;           // float2 per stored vector
+        float2 *Vd = reinterpret_cast<float2 *>(w.V);   // (m+1) vectors
+        int rc = run(K_SCALE, 1, 16.0 * dn + vb * dn, 2.0 * dn,
+                     [&] { return dst_k_split_f64_df(n, r, w.nrm + rslot, Vd, s, vlo); });
         if (rc) return rc;
         Hess hs(m);
         hs.start(rnorm);
         bool breakdown = false;
         int k = 0;
         for (int j = 0; j < m; ++j) {
-            float2 *vj = Vd + (size_t)j * 2 * n;
-            float2 *wv = Vd + (size_t)(j + 1) * 2 * n;
+            float2 *vj = Vd + (size_t)j * vs;
+            float2 *wv = Vd + (size_t)(j + 1) * vs;
             const int nv = j + 1;
             // FP32 apply straight from the hi plane of v_j into the hi plane of w
             if ((rc = run(K_APPLY32, 1, 16.0 * dn, 0.0,
                           [&] { return dst_internal_apply(mesh, DST_FP32, vj, wv, s); })))
                 return rc;
-            if ((rc = run(K_PROJECT, 1, 16.0 * dn * nv + 8.0 * dn, 8.0 * dn * nv,
+            if ((rc = run(K_PROJECT, 1, vb * dn * nv + 8.0 * dn, 8.0 * dn * nv,
                           [&] { return dst_k_project_df(n, nv, Vd, wv, true, w.h1, w.partials_c, nblk_proj, s,
-                                                        w.nrm + 3, w.partials_r, nullptr, w.tickets); })))
+                                                        w.nrm + 3, w.partials_r, nullptr, w.tickets, vlo); })))
                 return rc;
-            if ((rc = run(K_UPDATE, 1, 16.0 * dn * nv + 24.0 * dn, 8.0 * dn * nv,
+            if ((rc = run(K_UPDATE, 1, vb * dn * nv + 8.0 * dn + vb * dn, 8.0 * dn * nv,
                           [&] { return dst_k_update_df(n, nv, Vd, w.h1, wv, true, w.nrm, w.partials_r, nblk, s,
-                                                       nullptr, nullptr, w.tickets + 1); })))
+                                                       nullptr, nullptr, w.tickets + 1, vlo); })))
                 return rc;
             // second pass, gated on the device by the DGKS test unless always on (CGS2)
             const double *gate = ortho == 1 ? nullptr : w.nrm;
             const double g2 = gate ? 0.0 : 1.0;
-            if ((rc = run(K_PROJECT, 1, g2 * 16.0 * dn * (nv + 1), g2 * 8.0 * dn * nv,
-                          [&] { return dst_k_project_df(n, nv, Vd, wv, false, w.h2, w.partials_c, nblk_proj, s,
-                                                        nullptr, nullptr, gate, w.tickets); })))
+            if ((rc = run(K_PROJECT, 1, g2 * vb * dn * (nv + 1), g2 * 8.0 * dn * nv,
+                          [&] { return dst_k_project_df(n, nv, Vd, wv, !vlo, w.h2, w.partials_c, nblk_proj, s,
+                                                        nullptr, nullptr, gate, w.tickets, vlo); })))
                 return rc;
-            if ((rc = run(K_UPDATE, 1, g2 * 16.0 * dn * (nv + 2), g2 * 8.0 * dn * nv,
-                          [&] { return dst_k_update_df(n, nv, Vd, w.h2, wv, false, w.nrm, w.partials_r, nblk, s, gate,
-                                                       w.nrm + 6, w.tickets + 1); })))
+            if ((rc = run(K_UPDATE, 1, g2 * vb * dn * (nv + 2), g2 * 8.0 * dn * nv,
+                          [&] { return dst_k_update_df(n, nv, Vd, w.h2, wv, !vlo, w.nrm, w.partials_r, nblk, s, gate,
+                                                       w.nrm + 6, w.tickets + 1, vlo); })))
                 return rc;
-            if ((rc = run(K_SCALE, 1, 32.0 * dn, 6.0 * dn, [&] { return dst_k_scale_df(n, wv, w.nrm, s); }))) return rc;
+            if ((rc = run(K_SCALE, 1, 2.0 * vb * dn, 6.0 * dn, [&] { return dst_k_scale_df(n, wv, w.nrm, s, vlo); })))
+                return rc;
             if ((rc = read_step(nv))) return rc;
-            if (second_pass_ran() && gate) count_second_pass(nv, true);
+            if (second_pass_ran() && gate) count_second_pass(nv, vb);
             ++iters;
             if ((rc = take_column(hs, j, breakdown))) return rc;
             k = j + 1;
@@ -501,8 +507,8 @@ struct Solver {
         }
         hs.solve(k, w.host, 1.0);
         DST_CUDA_TRY(cudaMemcpyAsync(w.h1, w.host, sizeof(double2) * k, cudaMemcpyHostToDevice, s));
-        if ((rc = run(K_UPDATE, 1, 16.0 * dn * k + 32.0 * dn, 8.0 * dn * k,
-                      [&] { return dst_k_combine_df(n, k, Vd, w.h1, d, s); })))
+        if ((rc = run(K_UPDATE, 1, vb * dn * k + 32.0 * dn, 8.0 * dn * k,
+                      [&] { return dst_k_combine_df(n, k, Vd, w.h1, d, s, vlo); })))
             return rc;
         ++restarts;
         return DST_OK;
@@ -589,7 +595,7 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
         }
         // df32 Gram-Schmidt needs the correction to be one cycle from d = 0;
         // the r64 residual norm^2 must sit in nrm[2] for the first split
-        const bool use_df = o.mixed_ortho == 0 && o.inner_cycles == 1;
+        const bool use_df = o.mixed_ortho != 1 && o.inner_cycles == 1;
         if (!o.use_initial_guess) {
             DST_CUDA_TRY(cudaMemcpyAsync(sv.w.nrm + 2, sv.w.nrm + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
         }
@@ -600,7 +606,7 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
             DST_CUDA_TRY(cudaMemsetAsync(sv.w.d, 0, sizeof(double2) * n, s));
             const double itol = std::max(o.inner_rtol * rnorm, 0.5 * tol);
             if (use_df)
-                rc = sv.cycle_df(sv.w.d, sv.w.r64, 2, rnorm, itol, o.max_iters);
+                rc = sv.cycle_df(sv.w.d, sv.w.r64, 2, rnorm, itol, o.max_iters, o.mixed_ortho == 0);
             else
                 rc = sv.gmres(DST_FP32, sv.w.d, sv.w.r64, true, itol, o.max_iters, inner_beta,
                               o.inner_cycles > 0 ? o.inner_cycles : 0x7fffffff);
@@ -644,7 +650,7 @@ extern "C" int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, 
     if (opts) o = *opts;
     if (!mesh || !psi || o.restart < 1 || o.restart > DST_MAX_VEC - 1 || o.max_iters < 0 || !(o.rtol >= 0) ||
         (o.mixed_precision && (!(o.inner_rtol > 0) || o.max_refine < 1)) || o.ortho < 0 || o.ortho > 1 ||
-        o.mixed_ortho < 0 || o.mixed_ortho > 1 || o.inner_cycles < 0 || o.method < 0 || o.method > 1 ||
+        o.mixed_ortho < 0 || o.mixed_ortho > 2 || o.inner_cycles < 0 || o.method < 0 || o.method > 1 ||
         (o.method == 1 && o.mixed_precision)) {
         rc = DST_ERR_ARG;
     } else if (!mesh->d_psi0) {

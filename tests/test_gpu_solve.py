@@ -110,11 +110,12 @@ def test_plane_wave_config_solution(torch, B):
     assert 5.0e-5 < rel_l2(x, ex) < 6.5e-5
 
 
-@pytest.mark.parametrize("mixed_ortho", [0, 1])
+@pytest.mark.parametrize("mixed_ortho", [0, 1, 2])
 @pytest.mark.parametrize("d,n_el,bc", [(1, [64, 1, 1, 64], [P]), (2, [12, 10, 1, 14], [P, P]),
                                        (3, [5, 4, 4, 5], [P, D, D])])
 def test_mixed_precision_refinement(torch, B, d, n_el, bc, mixed_ortho):
-    """FP32 apply + FP64 refinement, inner Gram-Schmidt in double-FP32 (0) or FP64 (1)."""
+    """FP32 apply + FP64 refinement, inner Gram-Schmidt in double-FP32 (0), FP64 (1)
+    or compensated arithmetic on an FP32-stored basis (2)."""
     w = W.plane_wave_1p1(n=64) if d == 1 else W.random_mesh(d, n_el, bc, seed=80 + d)
     ref, _, _ = _exact(w)
     x, st = _solve(torch, B, w, restart=30, rtol=1e-12, max_iters=50000, mixed_precision=1,
