@@ -188,7 +188,7 @@ typedef struct {
     int ortho;              /* Gram-Schmidt: 0 = classical, second pass only when the DGKS test
                                asks (norm fell below 1/sqrt 2 of its value before the pass);
                                1 = always two classical passes (CGS2) */
-    int mixed_ortho;        /* mixed only: arithmetic of the inner Gram-Schmidt.  0 = double-FP32
+    int mixed_ortho;        /* mixed only: arithmetic of the inner Gram-Schmidt (default 2).  0 = double-FP32
                                (basis stored as FP32 hi/lo planes, 48-bit significand, error-free
                                FP32 products and sums, FP64 reductions; needs inner_cycles = 1),
                                1 = native FP64 (FP64 basis),
@@ -234,7 +234,8 @@ typedef struct {
 /* Fill opts with the defaults (restart 30, max_iters 100000, rtol 1e-8,
  * FP64, inner_rtol 1e-4, max_refine 100000, zero initial guess, no
  * profiling, one inner cycle per refinement, selective reorthogonalisation,
- * double-FP32 inner Gram-Schmidt, GMRES). */
+ * inner Gram-Schmidt on an FP32-stored basis in compensated arithmetic,
+ * GMRES). */
 DST_API int dst_default_solve_opts(dst_solve_opts *opts);
 
 /*

@@ -20,11 +20,12 @@
 // float2 lo[n] (re, im interleaved in each plane).  The hi plane alone is the
 // vector rounded to FP32 - the input the FP32 operator apply reads directly.
 //
-// Kernels templated on VL = false work on a basis stored as the hi plane
-// alone (8 bytes per complex entry, half the traffic): the stored vectors are
-// FP32 numbers, but the products are still exact (TwoProd) and the sums
-// compensated, so inner products and updates keep FP64-class accuracy with
-// respect to the stored values; updated vectors are rounded to FP32 once.
+// A basis may instead be stored as the hi plane alone (8 bytes per complex
+// entry, half the traffic; VL = false in the templates, project_f32_kernel
+// and update_f32_kernel): the stored vectors are FP32 numbers, but the
+// products are still exact (TwoProd) and the sums compensated, so inner
+// products and updates keep FP64-class accuracy with respect to the stored
+// values; updated vectors are rounded to FP32 once.
 #include "blas.h"
 
 namespace dst {
@@ -128,7 +129,7 @@ __device__ __forceinline__ void cdot_acc(float vhr, float vhi, float vlr, float 
 // planes) and DF_GROUP basis vectors per sweep over its slice.
 // The last CTA to finish (atomic ticket) sums every CTA's partials in CTA
 // order and writes h (and ||w||^2): a deterministic single-kernel reduction.
-template <bool W_HI_ONLY, bool VL>
+template <bool W_HI_ONLY>
 __global__ void __launch_bounds__(DF_THREADS)
 project_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float2 *__restrict__ w,
                   double2 *__restrict__ partials, double *__restrict__ wnrm_partials, const double *gate,
@@ -158,11 +159,10 @@ project_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float
             float4 vh[DF_GROUP], vl[DF_GROUP];
 #pragma unroll
             for (int g = 0; g < DF_GROUP; ++g) {
-                vl[g] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (g < gv) {
-                    const float4 *vj = reinterpret_cast<const float4 *>(V + (int64_t)(j0 + g) * (VL ? 2 : 1) * n);
+                    const float4 *vj = reinterpret_cast<const float4 *>(V + (int64_t)(j0 + g) * 2 * n);
                     vh[g] = vj[q];
-                    if (VL) vl[g] = vj[(n >> 1) + q];
+                    vl[g] = vj[(n >> 1) + q];
                 }
             }
             if (j0 == 0) {
@@ -175,8 +175,8 @@ project_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float
 #pragma unroll
             for (int g = 0; g < DF_GROUP; ++g) {
                 if (g < gv) {
-                    cdot_acc<VL, !W_HI_ONLY>(vh[g].x, vh[g].y, vl[g].x, vl[g].y, a.x, a.y, al.x, al.y, re[g], im[g]);
-                    cdot_acc<VL, !W_HI_ONLY>(vh[g].z, vh[g].w, vl[g].z, vl[g].w, a.z, a.w, al.z, al.w, re[g], im[g]);
+                    cdot_acc<true, !W_HI_ONLY>(vh[g].x, vh[g].y, vl[g].x, vl[g].y, a.x, a.y, al.x, al.y, re[g], im[g]);
+                    cdot_acc<true, !W_HI_ONLY>(vh[g].z, vh[g].w, vl[g].z, vl[g].w, a.z, a.w, al.z, al.w, re[g], im[g]);
                 }
             }
         }
@@ -254,7 +254,7 @@ __device__ __forceinline__ void renorm(DfAcc &a) {
 // w <- w - sum_j V_j h_j in df32 (h given in FP64, split per CTA), and
 // partials of ||w||^2 after the update.  W_HI_ONLY: w's lo plane is read as
 // zero.  Two neighbouring entries per thread step, as in the projection.
-template <bool W_HI_ONLY, bool VL>
+template <bool W_HI_ONLY>
 __global__ void __launch_bounds__(DF_THREADS)
 update_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double2 *__restrict__ h,
                  float2 *__restrict__ w, double *__restrict__ nrm_partials, const double *gate,
@@ -283,36 +283,28 @@ update_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double
         ar1.hi = a.z; ar1.lo = al.z; ai1.hi = a.w; ai1.lo = al.w;
         // software pipelining: the planes of V_{j+1} are loaded before V_j is combined
         const float4 *v0 = reinterpret_cast<const float4 *>(V);
-        const int64_t vstride = (VL ? 2 : 1) * n;
-        float4 vh = v0[q], vl = VL ? v0[(n >> 1) + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 vh = v0[q], vl = v0[(n >> 1) + q];
         for (int j = 0; j < nvec; ++j) {
             float4 nh = vh, nl = vl;
             if (j + 1 < nvec) {
-                const float4 *vn = reinterpret_cast<const float4 *>(V + (int64_t)(j + 1) * vstride);
+                const float4 *vn = reinterpret_cast<const float4 *>(V + (int64_t)(j + 1) * 2 * n);
                 nh = vn[q];
-                if (VL) nl = vn[(n >> 1) + q];
+                nl = vn[(n >> 1) + q];
             }
             const float4 c = hs[j];
-            caxpy_sub<VL>(vh.x, vh.y, vl.x, vl.y, c, ar0, ai0);
-            caxpy_sub<VL>(vh.z, vh.w, vl.z, vl.w, c, ar1, ai1);
+            caxpy_sub(vh.x, vh.y, vl.x, vl.y, c, ar0, ai0);
+            caxpy_sub(vh.z, vh.w, vl.z, vl.w, c, ar1, ai1);
             vh = nh;
             vl = nl;
         }
         renorm(ar0); renorm(ai0); renorm(ar1); renorm(ai1);
         wh[q] = make_float4(ar0.hi, ai0.hi, ar1.hi, ai1.hi);
+        wl[q] = make_float4(ar0.lo, ai0.lo, ar1.lo, ai1.lo);
         float p, r;
-        if (VL) {
-            wl[q] = make_float4(ar0.lo, ai0.lo, ar1.lo, ai1.lo);
-            df_prod(ar0.hi, ar0.lo, ar0.hi, ar0.lo, p, r); nr.add(p, r);
-            df_prod(ai0.hi, ai0.lo, ai0.hi, ai0.lo, p, r); nr.add(p, r);
-            df_prod(ar1.hi, ar1.lo, ar1.hi, ar1.lo, p, r); nr.add(p, r);
-            df_prod(ai1.hi, ai1.lo, ai1.hi, ai1.lo, p, r); nr.add(p, r);
-        } else {        // the norm of the stored (rounded) vector
-            df_prod_t<false, false>(ar0.hi, 0.f, ar0.hi, 0.f, p, r); nr.add(p, r);
-            df_prod_t<false, false>(ai0.hi, 0.f, ai0.hi, 0.f, p, r); nr.add(p, r);
-            df_prod_t<false, false>(ar1.hi, 0.f, ar1.hi, 0.f, p, r); nr.add(p, r);
-            df_prod_t<false, false>(ai1.hi, 0.f, ai1.hi, 0.f, p, r); nr.add(p, r);
-        }
+        df_prod(ar0.hi, ar0.lo, ar0.hi, ar0.lo, p, r); nr.add(p, r);
+        df_prod(ai0.hi, ai0.lo, ai0.hi, ai0.lo, p, r); nr.add(p, r);
+        df_prod(ar1.hi, ar1.lo, ar1.hi, ar1.lo, p, r); nr.add(p, r);
+        df_prod(ai1.hi, ai1.lo, ai1.hi, ai1.lo, p, r); nr.add(p, r);
     }
     const double s_ = dfwarp_sum(nr);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s_;
@@ -325,6 +317,294 @@ update_df_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double
         nrm_partials[blockIdx.x] = t;
     }
     // last CTA: ||w||^2 = sum over CTAs in CTA order (and bump the pass counter)
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    double t = 0.0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += 32) t += __ldcg(nrm_partials + k);
+    t = dwarp_sum(t);
+    if (threadIdx.x == 0) {
+        *nrm2 = t;
+        if (counter) *counter += 1.0;
+        *ticket = 0u;
+    }
+}
+
+// ---- FP32-stored basis: anchored error-free accumulation ------------------
+//
+// With the basis stored as single FP32 planes, the compensated sums of the
+// hi/lo kernels spend most of their instructions in TwoSum (6 additions per
+// term).  Here every thread first bounds the magnitude B of every partial sum
+// it will form (the basis vectors have unit 2-norm, so each of their
+// components is at most 1 in magnitude), picks a power of two sigma with
+// 4B < sigma <= 8B, and accumulates into hi = sigma + (partial sum), so hi
+// stays within [3/4, 5/4] sigma.  A product term a*b is added with one FMA,
+// s = fl(hi + a b); since s and hi are within a factor 2 of each other,
+// z = s - hi is exact (Sterbenz), so a b - z is exactly the rounding error
+// of that FMA, and fma(a, b, -z) delivers it rounded once to FP32 into a
+// plain lo.  Four instructions per term (two FMA, two additions) instead of
+// TwoProd + TwoSum; hi - sigma is exact at the end.  Anchoring to a fixed
+// power of two is the extraction idea of Rump, Ogita & Oishi's AccSum
+// (SIAM J. Sci. Comput. 31, 2008); the result has the accuracy of a
+// compensated dot product, about eps32^2 sigma per term.
+
+// power of two sigma with 4 b < sigma <= 8 b (b >= 0); +inf when b is not
+// finite or above 2^123, so that the results become NaN instead of wrong
+__device__ __forceinline__ float anchor_above(float b) {
+    const unsigned u = __float_as_uint(b * 1.001f) & 0x7f800000u;   // 2^floor(log2), 0 if subnormal
+    if (u >= (123u + 127u) << 23) return __int_as_float(0x7f800000);
+    return __uint_as_float(u + (3u << 23));
+}
+
+struct AnAcc {
+    float hi, lo;
+    __device__ __forceinline__ void init(float sigma) { hi = sigma; lo = 0.f; }
+    // += a b (|a b| <= sigma / 4)
+    __device__ __forceinline__ void madd(float a, float b) {
+        const float s_ = fmaf(a, b, hi);
+        const float z = s_ - hi;          // exact
+        lo += fmaf(a, b, -z);             // the FMA's rounding error
+        hi = s_;
+    }
+    // += x (|x| <= sigma / 4), FastTwoSum
+    __device__ __forceinline__ void add(float x) {
+        const float s_ = hi + x;
+        const float z = s_ - hi;
+        lo += x - z;
+        hi = s_;
+    }
+};
+
+// acc += conj(v) w for one complex entry, v and w FP32
+__device__ __forceinline__ void cdot_an(float vr, float vi, float ar, float ai, AnAcc &re, AnAcc &im) {
+    re.madd(vr, ar);
+    re.madd(vi, ai);
+    im.madd(vr, ai);
+    im.madd(-vi, ar);
+}
+
+// h_j = conj(V_j) w for an FP32-stored unit-norm basis and FP32 w, plus
+// ||w||^2; same slices, grouping and last-CTA reduction as project_df_kernel.
+__global__ void __launch_bounds__(DF_THREADS)
+project_f32_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float2 *__restrict__ w,
+                   double2 *__restrict__ partials, double *__restrict__ wnrm_partials, const double *gate,
+                   double2 *__restrict__ h, double *__restrict__ wnrm2, unsigned *__restrict__ ticket) {
+    if (gate != nullptr && !(gate[0] < 0.5 * gate[3])) {           // DGKS: no second pass needed
+        if (blockIdx.x == 0)
+            for (int j = threadIdx.x; j < nvec; j += DF_THREADS) h[j] = make_double2(0.0, 0.0);
+        return;
+    }
+    constexpr int NW = DF_THREADS / 32;
+    __shared__ double red[NW][2 * DST_MAX_VEC + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t b, e;
+    df_slice2(n, b, e);
+    const float4 *wh = reinterpret_cast<const float4 *>(w);
+    // the thread's entries once: ||w||^2 and the bound sum |w| (every partial
+    // sum of conj(v) w over these entries is at most that in magnitude)
+    DfAcc wn;
+    wn.zero();
+    float sw = 0.f;
+    for (int64_t i = b + 2 * threadIdx.x; i < e; i += 2 * DF_THREADS) {
+        const float4 a = wh[i >> 1];
+        float p, r;
+        p = a.x * a.x; r = fmaf(a.x, a.x, -p); wn.add(p, r);
+        p = a.y * a.y; r = fmaf(a.y, a.y, -p); wn.add(p, r);
+        p = a.z * a.z; r = fmaf(a.z, a.z, -p); wn.add(p, r);
+        p = a.w * a.w; r = fmaf(a.w, a.w, -p); wn.add(p, r);
+        sw += (fabsf(a.x) + fabsf(a.y)) + (fabsf(a.z) + fabsf(a.w));
+    }
+    const float sigma = anchor_above(sw);
+    const int64_t ub = b >> 1, ue = e >> 1;      // the slice in float4 units (two entries each)
+    for (int j0 = 0; j0 < nvec; j0 += DF_GROUP) {
+        const int gv = nvec - j0 < DF_GROUP ? nvec - j0 : DF_GROUP;
+        AnAcc re[DF_GROUP], im[DF_GROUP];
+#pragma unroll
+        for (int g = 0; g < DF_GROUP; ++g) { re[g].init(sigma); im[g].init(sigma); }
+        // two float4 units per thread and step, DF_THREADS apart
+        for (int64_t u = ub + threadIdx.x; u < ue; u += 2 * DF_THREADS) {
+            const int64_t u1 = u + DF_THREADS;
+            const bool two = u1 < ue;
+            const float4 a0 = wh[u];
+            const float4 a1 = two ? wh[u1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 v0h[DF_GROUP], v1h[DF_GROUP];
+#pragma unroll
+            for (int g = 0; g < DF_GROUP; ++g) {
+                v0h[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+                v1h[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g < gv) {
+                    const float4 *vj = reinterpret_cast<const float4 *>(V + (int64_t)(j0 + g) * n);
+                    v0h[g] = vj[u];
+                    if (two) v1h[g] = vj[u1];
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < DF_GROUP; ++g) {
+                if (g < gv) {
+                    cdot_an(v0h[g].x, v0h[g].y, a0.x, a0.y, re[g], im[g]);
+                    cdot_an(v0h[g].z, v0h[g].w, a0.z, a0.w, re[g], im[g]);
+                    cdot_an(v1h[g].x, v1h[g].y, a1.x, a1.y, re[g], im[g]);
+                    cdot_an(v1h[g].z, v1h[g].w, a1.z, a1.w, re[g], im[g]);
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < DF_GROUP; ++g) {
+            if (g < gv) {
+                DfAcc r_, i_;
+                r_.hi = re[g].hi - sigma; r_.lo = re[g].lo;      // exact differences
+                i_.hi = im[g].hi - sigma; i_.lo = im[g].lo;
+                const double sr = dfwarp_sum(r_), si = dfwarp_sum(i_);
+                if (lane == 0) { red[warp][2 * (j0 + g)] = sr; red[warp][2 * (j0 + g) + 1] = si; }
+            }
+        }
+    }
+    const double wsum = dfwarp_sum(wn);
+    if (lane == 0) red[warp][2 * DST_MAX_VEC] = wsum;
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * nvec; q += DF_THREADS) {
+        double s_ = 0.0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) s_ += red[k][q];
+        reinterpret_cast<double *>(partials + (int64_t)blockIdx.x * nvec)[q] = s_;
+    }
+    if (wnrm_partials && threadIdx.x == 0) {
+        double s_ = 0.0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) s_ += red[k][2 * DST_MAX_VEC];
+        wnrm_partials[blockIdx.x] = s_;
+    }
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const double *pd = reinterpret_cast<const double *>(partials);
+    for (int q = warp; q < 2 * nvec + 1; q += NW) {
+        double s_ = 0.0;
+        if (q < 2 * nvec) {
+            for (unsigned k = lane; k < gridDim.x; k += 32) s_ += __ldcg(pd + (size_t)k * 2 * nvec + q);
+        } else if (wnrm2) {
+            for (unsigned k = lane; k < gridDim.x; k += 32) s_ += __ldcg(wnrm_partials + k);
+        }
+        s_ = dwarp_sum(s_);
+        if (lane == 0) {
+            if (q < 2 * nvec) reinterpret_cast<double *>(h)[q] = s_;
+            else if (wnrm2) *wnrm2 = s_;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// acc -= v c for one complex entry (v FP32, c = (re_hi, re_lo, im_hi, im_lo))
+// (the lo halves of c are 2^-24 of the hi halves: their products go straight to lo)
+__device__ __forceinline__ void caxpy_an(float vr, float vi, const float4 &c, AnAcc &ar, AnAcc &ai) {
+    ar.madd(-vr, c.x); ar.lo = fmaf(-vr, c.y, ar.lo);     // - vr hr
+    ar.madd(vi, c.z);  ar.lo = fmaf(vi, c.w, ar.lo);      // + vi hi
+    ai.madd(-vr, c.z); ai.lo = fmaf(-vr, c.w, ai.lo);     // - vr hi
+    ai.madd(-vi, c.x); ai.lo = fmaf(-vi, c.y, ai.lo);     // - vi hr
+}
+
+// w <- w - sum_j V_j h_j for an FP32-stored unit-norm basis and FP32 w (h in
+// FP64, split per CTA), rounded to FP32 once; partials of ||w||^2 of the
+// stored result.  Per entry the bound is |w component| + sum_j |h_j|_1.
+__global__ void __launch_bounds__(DF_THREADS)
+update_f32_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double2 *__restrict__ h,
+                  float2 *__restrict__ w, double *__restrict__ nrm_partials, const double *gate,
+                  double *__restrict__ nrm2, double *__restrict__ counter, unsigned *__restrict__ ticket) {
+    if (gate != nullptr && !(gate[0] < 0.5 * gate[3])) return;     // DGKS: no second pass needed
+    constexpr int NW = DF_THREADS / 32;
+    __shared__ float4 hs[DST_MAX_VEC];     // (re_hi, re_lo, im_hi, im_lo)
+    __shared__ double red[NW];
+    __shared__ float h1_sh;
+    for (int j = threadIdx.x; j < nvec; j += DF_THREADS) {
+        const double2 c = h[j];
+        const float rh = (float)c.x, ih = (float)c.y;
+        hs[j] = make_float4(rh, (float)(c.x - (double)rh), ih, (float)(c.y - (double)ih));
+    }
+    if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (int j = threadIdx.x; j < nvec; j += 32) t += fabs(h[j].x) + fabs(h[j].y);
+        t = dwarp_sum(t);
+        if (threadIdx.x == 0) h1_sh = (float)t;
+    }
+    __syncthreads();
+    const float h1 = h1_sh;
+    int64_t b, e;
+    df_slice2(n, b, e);
+    float4 *wh = reinterpret_cast<float4 *>(w);
+    const float4 *v0 = reinterpret_cast<const float4 *>(V);
+    const int64_t vs = n >> 1;           // float4 per stored vector
+    const int64_t ub = b >> 1, ue = (e + 1) >> 1;     // the slice in float4 units (two entries each)
+    DfAcc nr;
+    nr.zero();
+    // two units per thread and step, DF_THREADS apart: two independent loads
+    // of every basis vector in flight
+    for (int64_t u = ub + threadIdx.x; u < ue; u += 2 * DF_THREADS) {
+        const int64_t u1 = u + DF_THREADS;
+        const bool two = u1 < ue;
+        const float4 a0 = wh[u];
+        const float4 a1 = two ? wh[u1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float s0 =
+            anchor_above(fmaxf(fmaxf(fabsf(a0.x), fabsf(a0.y)), fmaxf(fabsf(a0.z), fabsf(a0.w))) + h1);
+        const float s1 =
+            anchor_above(fmaxf(fmaxf(fabsf(a1.x), fabsf(a1.y)), fmaxf(fabsf(a1.z), fabsf(a1.w))) + h1);
+        AnAcc acc[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { acc[k].init(s0); acc[4 + k].init(s1); }
+        acc[0].add(a0.x); acc[1].add(a0.y); acc[2].add(a0.z); acc[3].add(a0.w);
+        acc[4].add(a1.x); acc[5].add(a1.y); acc[6].add(a1.z); acc[7].add(a1.w);
+        float4 v0h = v0[u], v1h = two ? v0[u1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < nvec; ++j) {
+            float4 n0 = v0h, n1 = v1h;       // next vector in flight
+            if (j + 1 < nvec) {
+                const float4 *vn = v0 + (int64_t)(j + 1) * vs;
+                n0 = vn[u];
+                if (two) n1 = vn[u1];
+            }
+            const float4 c = hs[j];
+            caxpy_an(v0h.x, v0h.y, c, acc[0], acc[1]);
+            caxpy_an(v0h.z, v0h.w, c, acc[2], acc[3]);
+            caxpy_an(v1h.x, v1h.y, c, acc[4], acc[5]);
+            caxpy_an(v1h.z, v1h.w, c, acc[6], acc[7]);
+            v0h = n0;
+            v1h = n1;
+        }
+        const float4 o0 = make_float4((acc[0].hi - s0) + acc[0].lo, (acc[1].hi - s0) + acc[1].lo,
+                                      (acc[2].hi - s0) + acc[2].lo, (acc[3].hi - s0) + acc[3].lo);
+        const float4 o1 = make_float4((acc[4].hi - s1) + acc[4].lo, (acc[5].hi - s1) + acc[5].lo,
+                                      (acc[6].hi - s1) + acc[6].lo, (acc[7].hi - s1) + acc[7].lo);
+        wh[u] = o0;
+        if (two) wh[u1] = o1;
+        float p, r;
+        p = o0.x * o0.x; r = fmaf(o0.x, o0.x, -p); nr.add(p, r);
+        p = o0.y * o0.y; r = fmaf(o0.y, o0.y, -p); nr.add(p, r);
+        p = o0.z * o0.z; r = fmaf(o0.z, o0.z, -p); nr.add(p, r);
+        p = o0.w * o0.w; r = fmaf(o0.w, o0.w, -p); nr.add(p, r);
+        if (two) {
+            p = o1.x * o1.x; r = fmaf(o1.x, o1.x, -p); nr.add(p, r);
+            p = o1.y * o1.y; r = fmaf(o1.y, o1.y, -p); nr.add(p, r);
+            p = o1.z * o1.z; r = fmaf(o1.z, o1.z, -p); nr.add(p, r);
+            p = o1.w * o1.w; r = fmaf(o1.w, o1.w, -p); nr.add(p, r);
+        }
+    }
+    const double s_ = dfwarp_sum(nr);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s_;
+    __syncthreads();
+    if (!nrm_partials) return;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) t += red[k];
+        nrm_partials[blockIdx.x] = t;
+    }
     __shared__ bool last;
     __threadfence();
     __syncthreads();
@@ -435,11 +715,11 @@ int dst_k_project_df(int64_t n, int nvec, const float2 *V, const float2 *w, bool
     if (!vlo && !w_hi_only) return DST_ERR_ARG;     // an FP32-stored basis has no lo planes at all
     double *wp = wnrm2 ? wnrm_partials : nullptr;
     if (!vlo)
-        project_df_kernel<true, false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wp, gate, h, wnrm2, ticket);
+        project_f32_kernel<<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wp, gate, h, wnrm2, ticket);
     else if (w_hi_only)
-        project_df_kernel<true, true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wp, gate, h, wnrm2, ticket);
+        project_df_kernel<true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wp, gate, h, wnrm2, ticket);
     else
-        project_df_kernel<false, true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wp, gate, h, wnrm2, ticket);
+        project_df_kernel<false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wp, gate, h, wnrm2, ticket);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
@@ -451,11 +731,11 @@ int dst_k_update_df(int64_t n, int nvec, const float2 *V, const double2 *h, floa
     if (!vlo && !w_hi_only) return DST_ERR_ARG;
     double *pp = nrm2 ? partials : nullptr;
     if (!vlo)
-        update_df_kernel<true, false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, pp, gate, nrm2, counter, ticket);
+        update_f32_kernel<<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, pp, gate, nrm2, counter, ticket);
     else if (w_hi_only)
-        update_df_kernel<true, true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, pp, gate, nrm2, counter, ticket);
+        update_df_kernel<true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, pp, gate, nrm2, counter, ticket);
     else
-        update_df_kernel<false, true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, pp, gate, nrm2, counter, ticket);
+        update_df_kernel<false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, h, w, pp, gate, nrm2, counter, ticket);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }

@@ -529,7 +529,7 @@ extern "C" int dst_default_solve_opts(dst_solve_opts *o) {
     o->use_initial_guess = 0;
     o->profile = 0;
     o->ortho = 0;
-    o->mixed_ortho = 0;
+    o->mixed_ortho = 2;
     o->method = 0;
     return DST_OK;
 }
@@ -541,7 +541,10 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     sv.mesh = mesh;
     sv.s = s;
     sv.nblk = dst_reduction_blocks(mesh->n_unknowns);
-    sv.nblk_proj = dst_projection_blocks(mesh->n_unknowns);
+    // an FP32-stored basis moves half the bytes per entry: slices of 2048
+    // entries, at most the 3 CTAs per SM that its projection's registers allow
+    sv.nblk_proj = mixed && o.mixed_ortho == 2 ? std::min(dst_reduction_blocks(mesh->n_unknowns), 3 * 152)
+                                               : dst_projection_blocks(mesh->n_unknowns);
     sv.ortho = o.ortho;
     int rc = setup_workspace(mesh, o.method == 1 ? std::max(o.restart, 5) : o.restart, mixed, sv.w);
     if (rc) return rc;
