@@ -42,9 +42,17 @@ struct Workspace {
     unsigned *tickets;     // [2] zero counters of the in-kernel reductions
     double2 *partials_c;
     double *partials_r;
+    double *cols;      // per Arnoldi step of a cycle: COL_STRIDE doubles (see col_* below)
     double *host;      // pinned, 2 * 2 * (m + 1) + 8 doubles
+    double *host_cols; // pinned, DST_MAX_VEC * COL_STRIDE doubles
     void *dev_base;
 };
+
+// One Arnoldi step's record in Workspace::cols: first-pass coefficients
+// (DST_MAX_VEC complex), second-pass coefficients (DST_MAX_VEC complex), and
+// 8 doubles: [0] ||w||^2 after the last pass, [3] before the first update,
+// [6] 1 if the second pass ran.
+constexpr int COL_STRIDE = 4 * DST_MAX_VEC + 8;
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -66,6 +74,7 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w) {
     const size_t otk = take(sizeof(unsigned) * 8);
     const size_t opc = take(sizeof(double2) * (size_t)nblk * DST_MAX_VEC);
     const size_t opr = take(sizeof(double) * (size_t)nblk);
+    const size_t ocols = take(sizeof(double) * (size_t)COL_STRIDE * DST_MAX_VEC);
     const size_t total = off;
     if (mesh->ws_bytes < total) {
         cudaFree(mesh->ws);
@@ -96,6 +105,7 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w) {
     w.tickets = (unsigned *)(base + otk);
     w.partials_c = (double2 *)(base + opc);
     w.partials_r = (double *)(base + opr);
+    w.cols = (double *)(base + ocols);
     return DST_OK;
 }
 
@@ -320,6 +330,17 @@ struct Solver {
     // Hessenberg column j from the host buffer (first pass at host[0], second
     // pass at host[2*MAXVEC], new norm^2 at host[4*MAXVEC]) into hs; returns
     // DST_ERR_NAN on a non-finite column.
+    int take_column(Hess &hs, int j, const double *c1, const double *c2, double hn2, bool &breakdown) {
+        const int nv = j + 1;
+        std::vector<cplx> col(nv);
+        for (int i = 0; i < nv; ++i) col[i] = cplx(c1[2 * i] + c2[2 * i], c1[2 * i + 1] + c2[2 * i + 1]);
+        double colsq = 0.0;
+        for (auto &c : col) colsq += std::norm(c);
+        if (!std::isfinite(hn2) || !std::isfinite(colsq)) return DST_ERR_NAN;
+        resid_est = hs.add_column(j, col.data(), std::sqrt(hn2));
+        breakdown = std::sqrt(hn2) <= 1e-14 * std::sqrt(colsq + hn2);
+        return DST_OK;
+    }
     int take_column(Hess &hs, int j, bool &breakdown) {
         const int nv = j + 1;
         std::vector<cplx> col(nv);
@@ -467,43 +488,63 @@ struct Solver {
         if (rc) return rc;
         Hess hs(m);
         hs.start(rnorm);
-        bool breakdown = false;
-        int k = 0;
-        for (int j = 0; j < m; ++j) {
+        // Every step of the cycle runs on the device (the second pass is gated
+        // there, norms and scaling too), so all steps are enqueued at once, each
+        // writing its own record in w.cols; the columns come back with one
+        // synchronisation per cycle.  Steps after the one that meets the
+        // tolerance (or breaks down) have run but are discarded.
+        const int steps = std::min(m, max_iters - iters);
+        if (steps < 1) return DST_OK;
+        DST_CUDA_TRY(cudaMemsetAsync(w.cols, 0, sizeof(double) * COL_STRIDE * steps, s));
+        for (int j = 0; j < steps; ++j) {
             float2 *vj = Vd + (size_t)j * vs;
             float2 *wv = Vd + (size_t)(j + 1) * vs;
             const int nv = j + 1;
+            double2 *c1 = reinterpret_cast<double2 *>(w.cols + (size_t)j * COL_STRIDE);
+            double2 *c2 = c1 + DST_MAX_VEC;
+            double *nr = w.cols + (size_t)j * COL_STRIDE + 4 * DST_MAX_VEC;
             // FP32 apply straight from the hi plane of v_j into the hi plane of w
             if ((rc = run(K_APPLY32, 1, 16.0 * dn, 0.0,
                           [&] { return dst_internal_apply(mesh, DST_FP32, vj, wv, s); })))
                 return rc;
             if ((rc = run(K_PROJECT, 1, vb * dn * nv + 8.0 * dn, 8.0 * dn * nv,
-                          [&] { return dst_k_project_df(n, nv, Vd, wv, true, w.h1, w.partials_c, nblk_proj, s,
-                                                        w.nrm + 3, w.partials_r, nullptr, w.tickets, vlo); })))
+                          [&] { return dst_k_project_df(n, nv, Vd, wv, true, c1, w.partials_c, nblk_proj, s,
+                                                        nr + 3, w.partials_r, nullptr, w.tickets, vlo); })))
                 return rc;
             if ((rc = run(K_UPDATE, 1, vb * dn * nv + 8.0 * dn + vb * dn, 8.0 * dn * nv,
-                          [&] { return dst_k_update_df(n, nv, Vd, w.h1, wv, true, w.nrm, w.partials_r, nblk, s,
+                          [&] { return dst_k_update_df(n, nv, Vd, c1, wv, true, nr, w.partials_r, nblk, s,
                                                        nullptr, nullptr, w.tickets + 1, vlo); })))
                 return rc;
             // second pass, gated on the device by the DGKS test unless always on (CGS2)
-            const double *gate = ortho == 1 ? nullptr : w.nrm;
+            const double *gate = ortho == 1 ? nullptr : nr;
             const double g2 = gate ? 0.0 : 1.0;
             if ((rc = run(K_PROJECT, 1, g2 * vb * dn * (nv + 1), g2 * 8.0 * dn * nv,
-                          [&] { return dst_k_project_df(n, nv, Vd, wv, !vlo, w.h2, w.partials_c, nblk_proj, s,
+                          [&] { return dst_k_project_df(n, nv, Vd, wv, !vlo, c2, w.partials_c, nblk_proj, s,
                                                         nullptr, nullptr, gate, w.tickets, vlo); })))
                 return rc;
             if ((rc = run(K_UPDATE, 1, g2 * vb * dn * (nv + 2), g2 * 8.0 * dn * nv,
-                          [&] { return dst_k_update_df(n, nv, Vd, w.h2, wv, !vlo, w.nrm, w.partials_r, nblk, s, gate,
-                                                       w.nrm + 6, w.tickets + 1, vlo); })))
+                          [&] { return dst_k_update_df(n, nv, Vd, c2, wv, !vlo, nr, w.partials_r, nblk, s, gate,
+                                                       nr + 6, w.tickets + 1, vlo); })))
                 return rc;
-            if ((rc = run(K_SCALE, 1, 2.0 * vb * dn, 6.0 * dn, [&] { return dst_k_scale_df(n, wv, w.nrm, s, vlo); })))
+            if ((rc = run(K_SCALE, 1, 2.0 * vb * dn, 6.0 * dn, [&] { return dst_k_scale_df(n, wv, nr, s, vlo); })))
                 return rc;
-            if ((rc = read_step(nv))) return rc;
-            if (second_pass_ran() && gate) count_second_pass(nv, vb);
+        }
+        DST_CUDA_TRY(cudaMemcpyAsync(w.host_cols, w.cols, sizeof(double) * COL_STRIDE * steps,
+                                     cudaMemcpyDeviceToHost, s));
+        if ((rc = sync())) return rc;
+        bool breakdown = false;
+        int k = 0;
+        for (int j = 0; j < steps; ++j) {
+            const double *c1 = w.host_cols + (size_t)j * COL_STRIDE;
+            const double *nr = c1 + 4 * DST_MAX_VEC;
+            if (nr[6] > 0.0) {
+                ++reorths;
+                if (ortho != 1) count_second_pass(j + 1, vb);
+            }
             ++iters;
-            if ((rc = take_column(hs, j, breakdown))) return rc;
+            if ((rc = take_column(hs, j, c1, c1 + 2 * DST_MAX_VEC, nr[0], breakdown))) return rc;
             k = j + 1;
-            if (breakdown || resid_est <= tol_abs || iters >= max_iters) break;
+            if (breakdown || resid_est <= tol_abs) break;
         }
         hs.solve(k, w.host, 1.0);
         DST_CUDA_TRY(cudaMemcpyAsync(w.h1, w.host, sizeof(double2) * k, cudaMemcpyHostToDevice, s));
@@ -550,12 +591,14 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     if (rc) return rc;
     static thread_local double *pinned = nullptr;
     if (!pinned) {
-        if (cudaMallocHost(&pinned, sizeof(double) * (8 * DST_MAX_VEC + 16)) != cudaSuccess) {
+        const size_t nd = 8 * DST_MAX_VEC + 16 + (size_t)COL_STRIDE * DST_MAX_VEC;
+        if (cudaMallocHost(&pinned, sizeof(double) * nd) != cudaSuccess) {
             pinned = nullptr;
             return DST_ERR_OOM;
         }
     }
     sv.w.host = pinned;
+    sv.w.host_cols = pinned + 8 * DST_MAX_VEC + 16;
     const int64_t n = mesh->n_unknowns;
     // b = -D_w21 psi0 and ||b||
     sv.prof.on = o.profile != 0;
