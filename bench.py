@@ -4,7 +4,9 @@
 One step = one whole solve of the 2+1 Zitterbewegung workload (96 x 96 space
 x 96 time Q1 elements, 2-component spinor, 1,769,472 complex unknowns) to
 relative residual 1e-8: right-hand side, FP32 operator applies inside GMRES(30),
-FP64 CGS2 orthogonalisation, Givens/least squares, FP64 iterative refinement.
+classical Gram-Schmidt with a selective second pass on an FP32-stored Krylov
+basis in compensated (FP64-class) arithmetic, FP64 Givens/least squares, FP64
+residuals and iterative refinement.
 Inputs are resident in HBM when the timed region starts; the GMRES basis
 (31 x 28 MB) exceeds L2, so no L2 flush is needed between steps.
 
@@ -15,6 +17,7 @@ timed solves, the end-to-end time through the C ABI with host buffers, and the
 FP64 CPU oracle timed on the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       python bench.py --ncu-case solve60|apply32_zb|apply32_klein|apply64_klein  (ncu capture cases)
 N > 1 runs under torch.distributed.run: independent replicas, one per GPU.
 """
 
@@ -42,9 +45,10 @@ SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_SM = 4.0     # 2 FP64 FMA per clock per SM (1/64 of the FP32 rate)
 FP32_FLOP_PER_CLK_SM = 256.0   # 128 FP32 FMA per clock per SM
 CLASSES = ("apply64", "apply32", "cast", "project", "update", "scale", "misc", "rhs")
-# DRAM read+write bytes per algorithmic byte of the df32 projection, from one ncu capture
-# (profiles/project_df_traffic_zb_2p1.md); valid for project_df_kernel as committed with it.
-PROJECT_DF_TRAFFIC_RATIO = 1.087
+# DRAM read+write bytes per algorithmic byte of the projection / update on the FP32-stored
+# basis, from one ncu capture of each (profiles/gram_schmidt_f32_zb_2p1.md); valid for
+# project_f32_kernel / update_f32_kernel as committed with that file (None: not captured).
+TRAFFIC_RATIO = {"project": 1.040, "update": 0.992}
 
 
 def measured_peaks():
@@ -126,7 +130,7 @@ CONFIG = {"workload": "zb_2p1: 2+1 Zitterbewegung packet (sigma 0.5, p0 (2,0), s
                       "unknowns; GMRES(30) with FP32 operator apply inside FP64 iterative refinement to "
                       "rel. resid 1e-8",
           "unknowns": 1769472, "rtol": RTOL, "restart": RESTART, "inner_rtol": INNER_RTOL,
-          "l2": "working set > L2 (GMRES basis 31 x 28 MB), no flush", "parallelism": "replicas"}
+          "l2": "working set > L2 (FP32 GMRES basis 31 x 14 MB = 439 MB), no flush", "parallelism": "replicas"}
 
 
 class ClockSampler:
@@ -218,6 +222,32 @@ def time_apply(torch, B, mesh, prec, n, iters=40):
     return ms, 2.0 * n * esz / (ms * 1e-3) / 1e9
 
 
+NCU_CASES = ("solve60", "apply32_zb", "apply32_klein", "apply64_klein")
+
+
+def run_ncu_case(case):
+    """Small fixed launches for ncu captures (nothing timed, nothing printed as a bench line).
+
+    solve60: the first 60 Arnoldi steps (two GMRES(30) cycles) of the bench's mixed solve;
+    apply32_zb / apply32_klein / apply64_klein: 12 operator applies on the 96^2 x 96 bench
+    mesh or the 48^3 x 48 3+1 Klein mesh, over rotating buffers.
+    """
+    import torch
+    from paper_2103_14588_gb300 import binding as B
+    torch.cuda.set_device(0)
+    w = W.klein_3p1(p0=1.05) if case.endswith("klein") else W.zb_2p1()
+    with B.Mesh.from_workload(w) as m:
+        if case == "solve60":
+            psi = torch.zeros(m.n_unknowns, dtype=torch.complex128, device="cuda")
+            st = B.dst_solve(m.handle, {"restart": RESTART, "rtol": RTOL, "max_iters": 60, "mixed_precision": 1}, psi)
+            torch.cuda.synchronize()
+            print("solve60: %d steps, status %d, %d second passes" % (st["iters"], st["status"], st["reorths"]))
+        else:
+            prec = B.DST_FP32 if case.startswith("apply32") else B.DST_FP64
+            ms, gbs = time_apply(torch, B, m.handle, prec, m.n_unknowns, iters=12)
+            print("%s: %.1f us per apply" % (case, 1e3 * ms))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -225,7 +255,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", choices=NCU_CASES, help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
+    if args.ncu_case:
+        run_ncu_case(args.ncu_case)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -306,8 +340,8 @@ def main():
     fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s at max clock
     dom = max(CLASSES, key=lambda k: tot[k][0])
     d_ms, d_l, d_b, d_f = tot[dom]
-    # in the timed (mixed, double-FP32 Gram-Schmidt) solve only the FP64 operator
-    # apply is bound by the FP64 pipe; every other class streams HBM
+    # in the timed mixed solve only the FP64 operator apply is bound by the FP64
+    # pipe; every other class streams HBM
     fp64_classes = ("apply64",)
     if dom in fp64_classes and d_f > 0:
         ach = d_f / (d_ms * 1e-3) / 1e12
@@ -324,9 +358,9 @@ def main():
             # per step one first-pass launch plus one gated second pass, which moves data
             # only when it runs (reorths); achieved = bytes per launch / time per launch
             launches_ran = sum(s["iters"] + s["reorths"] for s in stats)
-        if dom == "project" and PROJECT_DF_TRAFFIC_RATIO:
+        if TRAFFIC_RATIO.get(dom):
             # average algorithmic bytes per launch that ran times the measured DRAM/algorithmic ratio
-            traffic = PROJECT_DF_TRAFFIC_RATIO * d_b / max(launches_ran, 1)
+            traffic = TRAFFIC_RATIO[dom] * d_b / max(launches_ran, 1)
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": traffic, "traffic_unit": "bytes per launch", "peak_kind": hbm_kind,
                 "algorithmic_bytes_per_launch": d_b / max(launches_ran, 1),
@@ -383,7 +417,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 apply + f64 orthogonalisation/refinement", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 apply and Krylov basis; df32 (compensated f32) Gram-Schmidt; f64 residual, Givens, refinement", "data": "synthetic",
         "config": CONFIG,
         "time_to_solution_s": t_ms * 1e-3 / args.steps,
         "solve": {"iters": stats[-1]["iters"], "restarts": stats[-1]["restarts"],

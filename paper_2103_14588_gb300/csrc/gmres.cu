@@ -115,29 +115,42 @@ enum { K_APPLY64 = 0, K_APPLY32, K_CAST, K_PROJECT, K_UPDATE, K_SCALE, K_MISC, K
 // Per-class accounting of launches, algorithmic bytes / flops and, when
 // profiling, device time from CUDA events recorded around each launch on the
 // solver's stream (harvested at the solver's host synchronisation points).
+// Inside a chain of launches with nothing else enqueued between them (the
+// steps of a cycle) one event marks both the end of a launch and the start of
+// the next, half the events of separate brackets.
 struct Prof {
     bool on = false;
+    bool chain = false;      // the previous launch's end event may open the next one
     double ms[K_NCLASS] = {}, launches[K_NCLASS] = {}, bytes[K_NCLASS] = {}, flops[K_NCLASS] = {};
-    struct Pending { int cls; cudaEvent_t a, b; };
+    struct Pending { int cls; int a, b; };     // indices into line
     std::vector<Pending> pending;
+    std::vector<cudaEvent_t> line;             // events recorded since the last harvest
     std::vector<cudaEvent_t> pool;
+    int last = -1;                             // line index of the previous launch's end
     cudaEvent_t get() {
         if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
         cudaEvent_t e = nullptr;
         cudaEventCreate(&e);
         return e;
     }
+    int mark(cudaStream_t s) {
+        cudaEvent_t e = get();
+        cudaEventRecord(e, s);
+        line.push_back(e);
+        return (int)line.size() - 1;
+    }
     void harvest() {
         for (auto &p : pending) {
             float t = 0.f;
-            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.cls] += t;
-            pool.push_back(p.a);
-            pool.push_back(p.b);
+            if (cudaEventElapsedTime(&t, line[p.a], line[p.b]) == cudaSuccess) ms[p.cls] += t;
         }
+        for (auto e : line) pool.push_back(e);
+        line.clear();
         pending.clear();
+        last = -1;
     }
     ~Prof() {
-        for (auto &p : pending) { pool.push_back(p.a); pool.push_back(p.b); }
+        for (auto e : line) pool.push_back(e);
         for (auto e : pool) cudaEventDestroy(e);
     }
 };
@@ -212,13 +225,13 @@ struct Solver {
     // Run one launcher (nk kernels) of class cls with its algorithmic bytes / flops.
     template <typename F>
     int run(int cls, int nk, double nbytes, double nflops, F &&launch) {
-        cudaEvent_t a = nullptr, b = nullptr;
-        if (prof.on) { a = prof.get(); cudaEventRecord(a, s); }
+        int a = -1;
+        if (prof.on) a = prof.chain && prof.last >= 0 ? prof.last : prof.mark(s);
         int rc = launch();
         if (prof.on) {
-            b = prof.get();
-            cudaEventRecord(b, s);
+            const int b = prof.mark(s);
             prof.pending.push_back({cls, a, b});
+            prof.last = b;
         }
         prof.launches[cls] += nk;
         prof.bytes[cls] += nbytes;
@@ -496,6 +509,8 @@ struct Solver {
         const int steps = std::min(m, max_iters - iters);
         if (steps < 1) return DST_OK;
         DST_CUDA_TRY(cudaMemsetAsync(w.cols, 0, sizeof(double) * COL_STRIDE * steps, s));
+        prof.chain = true;          // only kernels are enqueued until the loop ends
+        prof.last = -1;
         for (int j = 0; j < steps; ++j) {
             float2 *vj = Vd + (size_t)j * vs;
             float2 *wv = Vd + (size_t)(j + 1) * vs;
@@ -529,6 +544,7 @@ struct Solver {
             if ((rc = run(K_SCALE, 1, 2.0 * vb * dn, 6.0 * dn, [&] { return dst_k_scale_df(n, wv, nr, s, vlo); })))
                 return rc;
         }
+        prof.chain = false;
         DST_CUDA_TRY(cudaMemcpyAsync(w.host_cols, w.cols, sizeof(double) * COL_STRIDE * steps,
                                      cudaMemcpyDeviceToHost, s));
         if ((rc = sync())) return rc;
