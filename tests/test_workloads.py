@@ -42,3 +42,15 @@ def test_klein_potential_step():
     V = w.V.reshape(8, 8, 8)
     assert np.all(V[:, :, :4] == 0.0) and np.all(V[:, :, 4:] == 2.5)
     assert w.psi0.shape == (8, 8, 7, 4)
+
+
+def test_sommerfeld_potential_and_packet():
+    """The 1+1 Sommerfeld workload samples Eq. 23 at the element centroids and
+    starts a positive-energy packet far from the Dirichlet walls."""
+    from oracle import exact as EX, mesh as OM
+    w = W.sommerfeld_1p1(n=64, nt=8, L=0.25)
+    om = OM.Mesh(w.d, w.n_el, w.lo, w.hi, w.bc)
+    assert np.allclose(w.V, EX.sommerfeld(om.element_centroids(0), 2.5, 0.0, 0.25), rtol=0, atol=1e-15)
+    assert w.psi0.shape == (1, 1, 63, 2)
+    dens = np.sum(np.abs(w.psi0) ** 2, axis=-1).ravel()
+    assert dens[0] < 1e-6 * dens.max() and dens[-1] < 1e-20 * dens.max()

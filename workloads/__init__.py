@@ -162,6 +162,22 @@ def klein_3p1(n=48, nt=48, seed=1, p0=None, V0=2.5, sigma=0.5, xc=-2.0, m=1.0):
                     {"p0": p0, "V0": V0, "seed": seed})
 
 
+def sommerfeld_1p1(n=256, nt=256, L=0.001, V0=2.5, p0=1.05, sigma=4.0, xc=-16.0, half=40.0, tf=40.0, m=1.0):
+    """1+1 Klein scattering at the Sommerfeld smooth step of Sec. 4.3, Eq. 23:
+    V(x) = V0 / 2 (1 + tanh(x / L)) sampled at the element centroids; a
+    positive-energy Gaussian packet (width sigma, centre xc, momentum p0) on
+    [-half, half] x [0, tf] with homogeneous Dirichlet walls far from the packet."""
+    n_el, lo, hi = [n, 1, 1, nt], [-half, 0, 0, 0], [half, 1, 1, tf]
+    bc = [DIRICHLET, PERIODIC, PERIODIC]
+    X, _, _ = _grid(1, n_el, lo, hi, bc)
+    up, _ = spinor_pm(1, [p0], m)
+    psi0 = np.exp(-(X - xc) ** 2 / (4 * sigma ** 2) + 1j * p0 * X)[..., None] * up
+    cx = element_centroids(n, lo[0], hi[0])
+    V = 0.5 * V0 * (1.0 + np.tanh(cx / L))
+    return Workload("sommerfeld_1p1_%dx%d_L%g" % (n, nt, L), 1, n_el, lo, hi, bc, m, V, psi0,
+                    {"p0": p0, "V0": V0, "L": L, "sigma": sigma})
+
+
 def random_mesh(d, n_el, bc, seed, with_potential=True, m=0.9):
     """Small random-data workload for parity tests (random psi0 and V)."""
     rng = np.random.default_rng(seed)
