@@ -469,14 +469,15 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
     };
 
     if (S::FULL) {
-        // every plane of the chunk in flight before the first is consumed
+        // every plane of the chunk in flight at once; one wait and one barrier,
+        // then the planes' independent loads and arithmetic can interleave
 #pragma unroll
         for (int i = 0; i < S::STAGES; ++i) issue_next(i);
+        cp_async_wait<0>();
+        __syncthreads();
 #pragma unroll
         for (int i = 0; i < S::STAGES; ++i) {
             if (i < nplanes) {
-                cp_async_wait_n(S::STAGES - 1 - i);
-                __syncthreads();
                 V GC[RY][NC], GM[RY][NC];
                 plane_fields(i, i, GC, GM);
                 accumulate(i, GC, GM);
