@@ -199,6 +199,9 @@ typedef struct {
     int method;             /* Krylov method: 0 = restarted GMRES(restart) (default),
                                1 = BiCGSTAB (van der Vorst 1992; FP64 only, mixed_precision
                                must be 0; iters counts BiCGSTAB steps of two applies each) */
+    int batch_cta_max;      /* dst_solve_batch only: meshes of at most this many unknowns are
+                               solved one CTA each inside a persistent kernel, larger ones by
+                               concurrent single-mesh solves; negative = automatic (default) */
 } dst_solve_opts;
 
 /* Kernel classes of dst_solve_stats' per-class arrays. */
@@ -248,6 +251,34 @@ DST_API int dst_default_solve_opts(dst_solve_opts *opts);
  */
 DST_API int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, dst_solve_stats *stats,
               void *stream);
+
+/*
+ * Batched solve: Algorithm 1 step 6 for `count` independent meshes at once,
+ * each psi[i] (DEVICE, complex FP64, meshes[i]'s n_unknowns, 16-byte aligned)
+ * receiving the solution of its own mesh.  Every mesh must be 1+1 or 2+1, live
+ * on the current device, carry initial data (else DST_ERR_STATE) and have an
+ * x-only potential or none (a potential varying along y is DST_ERR_ARG).
+ * Every mesh gets the mixed-precision refinement of dst_solve (FP64
+ * residual, one GMRES(restart) cycle per refinement with the FP32 operator
+ * apply, an FP32-stored basis and compensated Gram-Schmidt, FP64 Givens
+ * rotations).  Meshes of at most opts->batch_cta_max unknowns are solved by
+ * one CTA each inside a single persistent kernel launch per spatial dimension,
+ * without host involvement until all of them finish; larger meshes are solved
+ * by single-mesh solves running concurrently from worker threads, each on a
+ * stream of its own (the meshes must not be used by other threads meanwhile).
+ * Used from opts: restart (1..32), max_iters and max_refine (per mesh), rtol,
+ * inner_rtol, ortho, use_initial_guess, batch_cta_max; method must be 0;
+ * mixed_precision, inner_cycles, mixed_ortho and profile are ignored.  The
+ * persistent kernel's workspace (two FP64 and restart + 1 FP32 vectors per
+ * mesh) is stream-ordered; larger meshes keep their own workspaces as with
+ * dst_solve.  Synchronises `stream` before returning.  stats[i] (count entries, required) receives each mesh's steps,
+ * refinements, status and true residual; seconds is the wall time of the
+ * whole call.  Returns the most severe error status of any mesh (a mesh that
+ * did not converge reports DST_NOT_CONVERGED in its stats only), or
+ * DST_ERR_ARG / DST_ERR_STATE / DST_ERR_OOM / DST_ERR_CUDA for the call.
+ */
+DST_API int dst_solve_batch(int count, dst_mesh *const *meshes, const dst_solve_opts *opts, void *const *psi,
+                            dst_solve_stats *stats, void *stream);
 
 /*
  * Observables of a solution, per unknown time layer t = 1..N_t, by trapezoidal

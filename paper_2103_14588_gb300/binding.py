@@ -25,7 +25,7 @@ EXPORTED = (
     "dst_create_mesh", "dst_destroy_mesh", "dst_mesh_sizes", "dst_set_mass", "dst_set_potential",
     "dst_set_initial_data", "dst_build_rhs", "dst_apply_operator", "dst_arnoldi_project",
     "dst_arnoldi_update", "dst_default_solve_opts", "dst_solve", "dst_status_string",
-    "dst_last_error_detail", "dst_arnoldi_project_noalloc", "dst_observables",
+    "dst_last_error_detail", "dst_arnoldi_project_noalloc", "dst_observables", "dst_solve_batch",
 )
 
 
@@ -43,7 +43,7 @@ class dst_solve_opts(ctypes.Structure):
                 ("mixed_precision", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
                 ("profile", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("ortho", ctypes.c_int),
-                ("mixed_ortho", ctypes.c_int), ("method", ctypes.c_int)]
+                ("mixed_ortho", ctypes.c_int), ("method", ctypes.c_int), ("batch_cta_max", ctypes.c_int)]
 
 
 class dst_solve_stats(ctypes.Structure):
@@ -87,6 +87,7 @@ def _load():
         "dst_observables": (c_int, [vp, vp, c_double, vp, vp]),
         "dst_default_solve_opts": (c_int, [P(dst_solve_opts)]),
         "dst_solve": (c_int, [vp, P(dst_solve_opts), vp, P(dst_solve_stats), vp]),
+        "dst_solve_batch": (c_int, [c_int, P(vp), P(dst_solve_opts), P(vp), P(dst_solve_stats), vp]),
         "dst_status_string": (ctypes.c_char_p, [c_int]),
         "dst_last_error_detail": (ctypes.c_char_p, []),
     }
@@ -274,6 +275,33 @@ def dst_solve(mesh, opts, psi, stream=None):
     rc = _lib.dst_solve(mesh, ctypes.byref(o), p, ctypes.byref(st), _stream(stream, psi))
     _check(rc, "dst_solve")
     return st.as_dict()
+
+
+def dst_solve_batch(meshes, opts, psis, stream=None):
+    """Solve every mesh into its psi (complex128 CUDA tensors) in one batched call.
+
+    meshes: mesh handles; psis: one tensor per mesh.  Returns (status, list of
+    stats dicts); raises DstError on an error of the call itself.
+    """
+    import torch
+    n = len(meshes)
+    if n != len(psis) or n == 0:
+        raise ValueError("one psi per mesh, at least one mesh")
+    o = opts if isinstance(opts, dst_solve_opts) else dst_default_solve_opts()
+    if isinstance(opts, dict):
+        for k, v in opts.items():
+            setattr(o, k, v)
+    mh = (ctypes.c_void_p * n)(*[ctypes.c_void_p(h) for h in meshes])
+    pp = []
+    for h, t in zip(meshes, psis):
+        _, nu, _ = dst_mesh_sizes(h)
+        pp.append(_dev_ptr(t, torch.complex128, nu, "psi"))
+    pa = (ctypes.c_void_p * n)(*pp)
+    sts = (dst_solve_stats * n)()
+    rc = _lib.dst_solve_batch(n, mh, ctypes.byref(o), pa, sts, _stream(stream, *psis))
+    if rc < 0 and rc not in (DST_ERR_NAN,):
+        _check(rc, "dst_solve_batch")
+    return rc, [s_.as_dict() for s_ in sts]
 
 
 class Mesh:

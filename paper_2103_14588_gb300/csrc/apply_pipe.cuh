@@ -301,20 +301,20 @@ __device__ __forceinline__ void fields_std_rows(Get get, const StdConst<T> &sc, 
 
 // STD: every node of the mesh has the standard interior stencils on every axis
 // (no open axis), so the general-coefficient branch is not compiled in.
+// One CTA's work: output tile `tile` over the time chunk `chunk`, staged through
+// `ring` (PipeShape::SMEM bytes of shared memory), PipeShape::NTHR threads.
+// Ends with every copy complete; a caller that reuses the ring for another
+// tile synchronises the CTA first.
 template <int D, int NC, typename T, bool NOV, bool STD>
-__global__ void __launch_bounds__(PipeShape<D, NC, T>::NTHR,
-                                  sizeof(T) == 8 ? 1 : (D == 3 ? (STD ? 2 : 1) : 3))
-apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typename C2<T>::type *__restrict__ y,
-                  int64_t tiles_x, int64_t tiles_y) {
+__device__ __forceinline__ void apply_pipe_tile(const OpParams &p, const typename C2<T>::type *__restrict__ x,
+                                                typename C2<T>::type *__restrict__ y, int64_t tiles_x,
+                                                int64_t tiles_y, int64_t tile, int64_t chunk, char *ring) {
     using V = typename C2<T>::type;
     using S = PipeShape<D, NC, T>;
     using Tile = typename S::Tile;
     constexpr int RY = Tile::RY;
     constexpr int TYT = Tile::TY / RY;                  // threads along y
-    extern __shared__ __align__(16) char ring[];
 
-    const int64_t tile = blockIdx.x;
-    const int64_t chunk = blockIdx.y;
     const int64_t x0 = (tile % tiles_x) * Tile::TX;
     const int64_t y0 = ((tile / tiles_x) % tiles_y) * Tile::TY;
     const int64_t z0 = (tile / (tiles_x * tiles_y)) * Tile::TZ;
@@ -516,6 +516,15 @@ apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
     }
     cp_async_wait<0>();
     (void)any_valid;
+}
+
+template <int D, int NC, typename T, bool NOV, bool STD>
+__global__ void __launch_bounds__(PipeShape<D, NC, T>::NTHR,
+                                  sizeof(T) == 8 ? 1 : (D == 3 ? (STD ? 2 : 1) : 3))
+apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typename C2<T>::type *__restrict__ y,
+                  int64_t tiles_x, int64_t tiles_y) {
+    extern __shared__ __align__(16) char ring[];
+    apply_pipe_tile<D, NC, T, NOV, STD>(p, x, y, tiles_x, tiles_y, blockIdx.x, blockIdx.y, ring);
 }
 
 template <int D, int NC, typename T>

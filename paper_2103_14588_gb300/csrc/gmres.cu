@@ -588,6 +588,7 @@ extern "C" int dst_default_solve_opts(dst_solve_opts *o) {
     o->ortho = 0;
     o->mixed_ortho = 2;
     o->method = 0;
+    o->batch_cta_max = -1;
     return DST_OK;
 }
 

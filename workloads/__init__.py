@@ -178,6 +178,44 @@ def sommerfeld_1p1(n=256, nt=256, L=0.001, V0=2.5, p0=1.05, sigma=4.0, xc=-16.0,
                     {"p0": p0, "V0": V0, "L": L, "sigma": sigma})
 
 
+def batch_instances(count=64, seed=4, n1=(32, 256), n2=(16, 48)):
+    """Independent solves for the batched solver: each instance is 1+1 or 2+1
+    (probability 1/2 each), with element counts per axis (time included) drawn
+    uniformly from n1 (1+1) or n2 (2+1), mass U[0.5, 2], momentum U[-4, 4] along
+    x, a barrier of height U[0, 3] over x >= 0 (x-only potential), and a
+    positive-energy Gaussian packet of width 0.1 L at x = -L/4 on
+    [-L/2, L/2]^d x [0, L/2], L = 20, homogeneous Dirichlet in x, periodic in y.
+    All draws come from splitmix64(seed)."""
+    u = uniform01(seed, 8 * count)
+    out = []
+    L = 20.0
+    for i in range(count):
+        r = u[8 * i: 8 * i + 8]
+        d = 1 if r[0] < 0.5 else 2
+        lo_n, hi_n = n1 if d == 1 else n2
+        pick = lambda x: int(lo_n + min(int(x * (hi_n - lo_n + 1)), hi_n - lo_n))
+        nx, ny, nt = pick(r[1]), pick(r[2]), pick(r[3])
+        m = 0.5 + 1.5 * r[4]
+        p0 = -4.0 + 8.0 * r[5]
+        V0 = 3.0 * r[6]
+        n_el = [nx, ny if d == 2 else 1, 1, nt]
+        lo = [-L / 2, -L / 2 if d == 2 else 0.0, 0.0, 0.0]
+        hi = [L / 2, L / 2 if d == 2 else 1.0, 1.0, L / 2]
+        bc = [DIRICHLET, PERIODIC, PERIODIC]
+        X, Y, _ = _grid(d, n_el, lo, hi, bc)
+        pv = [p0] + ([0.0] if d == 2 else [])
+        up, _ = spinor_pm(d, pv, m)
+        sig = 0.1 * L
+        env = np.exp(-((X + L / 4) ** 2) / (4 * sig ** 2) + 1j * p0 * X)
+        psi0 = _unit_norm(env[..., None] * up, d, n_el, lo, hi)
+        cx = element_centroids(nx, lo[0], hi[0])
+        vx = np.where(cx >= 0.0, V0, 0.0)
+        V = np.tile(vx, n_el[1]) if d == 2 else vx
+        out.append(Workload("batch%03d_%dp1_%s" % (i, d, "x".join(str(k) for k in n_el[:d] + [nt])), d, n_el,
+                            lo, hi, bc, m, V, psi0, {"p0": p0, "V0": V0}))
+    return out
+
+
 def random_mesh(d, n_el, bc, seed, with_potential=True, m=0.9):
     """Small random-data workload for parity tests (random psi0 and V)."""
     rng = np.random.default_rng(seed)
