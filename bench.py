@@ -13,8 +13,9 @@ Inputs are resident in HBM when the timed region starts; the GMRES basis
 Also reported on the same line: the plain-FP64-GMRES time-to-solution of the
 same system, the standalone operator-apply bandwidth (rotating buffers > 2x L2),
 the roofline of the dominant kernel class measured with CUDA events inside the
-timed solves, the end-to-end time through the C ABI with host buffers, and the
-FP64 CPU oracle timed on the host cores.
+timed solves, the end-to-end time through the C ABI with host buffers, the
+FP64 CPU oracle timed on the host cores, and the throughput of the batched
+solve (dst_solve_batch) on two seeded sets of independent 1+1 / 2+1 solves.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
        python bench.py --ncu-case solve60|apply32_zb|apply32_klein|apply64_klein  (ncu capture cases)
@@ -248,6 +249,54 @@ def run_ncu_case(case):
             print("%s: %.1f us per apply" % (case, 1e3 * ms))
 
 
+BATCH_CASES = (
+    # name, count, 1+1 element range per axis, 2+1 element range per axis, sequential sample
+    ("tiny", 128, (24, 40), (8, 12), 16),
+    ("mixed", 64, (32, 256), (16, 48), 8),
+)
+
+
+def run_batch_bench(torch, B):
+    """Throughput of dst_solve_batch on seeded independent 1+1 / 2+1 solves
+    (workloads.batch_instances), against single-mesh mixed solves one after
+    another on an evenly spaced sample of the same instances (scaled to the count)."""
+    import time as _t
+    out = {}
+    opts = {"rtol": RTOL, "max_iters": 20000, "max_refine": 100000}
+    for name, count, n1, n2, sample in BATCH_CASES:
+        ws = W.batch_instances(count, 4, n1=n1, n2=n2)
+        meshes = [B.Mesh.from_workload(w) for w in ws]
+        psis = [torch.zeros(m.n_unknowns, dtype=torch.complex128, device="cuda") for m in meshes]
+        torch.cuda.synchronize()
+        t0 = _t.perf_counter()
+        rc, sts = B.dst_solve_batch([m.handle for m in meshes], opts, psis)
+        torch.cuda.synchronize()
+        tb = _t.perf_counter() - t0
+        idx = list(range(0, count, count // sample))[:sample]
+        q = torch.zeros(max(m.n_unknowns for m in meshes), dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t0 = _t.perf_counter()
+        seq_steps = 0
+        for i in idx:
+            seq_steps += B.dst_solve(meshes[i].handle, dict(opts, mixed_precision=1), q[:meshes[i].n_unknowns])["iters"]
+        torch.cuda.synchronize()
+        t_sample = _t.perf_counter() - t0
+        ts = t_sample * count / len(idx)
+        conv = sum(1 for st in sts if st["status"] == 0)
+        out[name] = {"instances": count, "unknowns_total": int(sum(m.n_unknowns for m in meshes)),
+                     "persistent_kernel_meshes": int(sum(m.n_unknowns <= 4096 for m in meshes)),
+                     "batch_solves_per_s": count / tb, "batch_s": tb,
+                     "sequential_solves_per_s": count / ts, "sequential_sample": len(idx),
+                     "speedup": ts / tb, "converged": conv, "status": rc,
+                     "arnoldi_steps": int(sum(st["iters"] for st in sts)),
+                     "batch_steps_per_s": sum(st["iters"] for st in sts) / tb,
+                     "sequential_steps_per_s": seq_steps / t_sample,
+                     "note": "solves capped at 20000 Arnoldi steps count as solves on both sides"}
+        for m in meshes:
+            m.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,6 +304,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve throughput cases")
     ap.add_argument("--ncu-case", choices=NCU_CASES, help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.ncu_case:
@@ -402,6 +452,8 @@ def main():
     e2e = {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(psi0_host.numel() * 16),
            "d2h_bytes_per_step": int(n * 16)}
 
+    batch = None if args.no_batch else run_batch_bench(torch, B)
+
     cpu = None
     if not args.no_cpu_baseline:
         sec_step = oracle_seconds_per_step(w, k=2)
@@ -431,6 +483,7 @@ def main():
                   "hbm_peak": hbm, "peak_kind": hbm_kind, "bytes_per_unknown": {"fp32": 16, "fp64": 32}},
         "roofline": roof,
         "kernels": kernels,
+        "batch": batch,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

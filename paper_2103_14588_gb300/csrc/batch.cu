@@ -443,7 +443,7 @@ using namespace dst;
 
 // Meshes up to this many unknowns go to the persistent one-CTA-per-mesh kernel
 // when opts->batch_cta_max is negative (automatic).
-constexpr int64_t BATCH_CTA_MAX_AUTO = 2048;
+constexpr int64_t BATCH_CTA_MAX_AUTO = 4096;
 constexpr int BATCH_WORKERS = 16;          // concurrent single-mesh solves (one stream each)
 
 extern "C" int dst_solve_batch(int count, dst_mesh *const *meshes, const dst_solve_opts *opts, void *const *psi,
