@@ -121,6 +121,7 @@ enum { K_APPLY64 = 0, K_APPLY32, K_CAST, K_PROJECT, K_UPDATE, K_SCALE, K_MISC, K
 struct Prof {
     bool on = false;
     bool chain = false;      // the previous launch's end event may open the next one
+    bool capturing = false;  // recording into a stream capture: events become graph nodes
     double ms[K_NCLASS] = {}, launches[K_NCLASS] = {}, bytes[K_NCLASS] = {}, flops[K_NCLASS] = {};
     struct Pending { int cls; int a, b; };     // indices into line
     std::vector<Pending> pending;
@@ -135,7 +136,8 @@ struct Prof {
     }
     int mark(cudaStream_t s) {
         cudaEvent_t e = get();
-        cudaEventRecord(e, s);
+        if (capturing) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+        else cudaEventRecord(e, s);
         line.push_back(e);
         return (int)line.size() - 1;
     }
@@ -143,6 +145,7 @@ struct Prof {
         for (auto &p : pending) {
             float t = 0.f;
             if (cudaEventElapsedTime(&t, line[p.a], line[p.b]) == cudaSuccess) ms[p.cls] += t;
+            else cudaGetLastError();
         }
         for (auto e : line) pool.push_back(e);
         line.clear();
@@ -208,6 +211,33 @@ struct Hess {
     }
 };
 
+struct Solver;
+
+// The captured CUDA graph of one full mixed GMRES cycle (see Solver::enqueue_cycle):
+// the executable graph, the per-class accounting one replay adds, and, when
+// profiling, the event pairs recorded inside the graph.
+struct CycleGraph {
+    bool ok = true;                      // false after a failed capture: launch directly
+    cudaGraphExec_t exec = nullptr;
+    double launches[K_NCLASS] = {}, bytes[K_NCLASS] = {}, flops[K_NCLASS] = {};
+    double total_bytes = 0.0;
+    std::vector<Prof::Pending> pending;  // indices into events
+    std::vector<cudaEvent_t> events;
+    int capture(Solver &sv, int steps, bool vlo);
+    void account(Solver &sv);
+    void harvest(Prof &p) {
+        for (auto &q : pending) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, events[q.a], events[q.b]) == cudaSuccess) p.ms[q.cls] += t;
+            else cudaGetLastError();
+        }
+    }
+    ~CycleGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (auto e : events) cudaEventDestroy(e);
+    }
+};
+
 struct Solver {
     dst_mesh *mesh;
     cudaStream_t s;
@@ -221,6 +251,7 @@ struct Solver {
     int ortho = 0;           // 0: DGKS selective second pass, 1: always two passes
     double resid_est = 0.0;
     Prof prof;
+    CycleGraph graph;
 
     // Run one launcher (nk kernels) of class cls with its algorithmic bytes / flops.
     template <typename F>
@@ -484,30 +515,16 @@ struct Solver {
         return DST_OK;
     }
 
-    // One GMRES(m) cycle for the correction equation A d = r (d = 0 on entry),
-    // FP32 operator apply on a df32 basis with df32 Gram-Schmidt: V_0 = r/||r||
-    // (||r||^2 in w.nrm[rslot]), d += V y at the end (FP64).
-    // vlo = false: the basis is stored in FP32 (hi planes only, 8 B per entry)
-    // and the same compensated kernels run on it.
-    int cycle_df(double2 *d, const double2 *r, int rslot, double rnorm, double tol_abs, int max_iters, bool vlo) {
-        const int m = w.m;
+    // The Arnoldi steps of one mixed cycle: a zeroed record per step, then per
+    // step the FP32 apply, both Gram-Schmidt passes (the second gated on the
+    // device) and the scaling, all on stream s.
+    int enqueue_steps(int steps, bool vlo) {
         const int64_t n = w.n;
         const double dn = (double)n;
-        const double vb = vlo ? 16.0 : 8.0;             // bytes per stored basis entry
-        const int64_t vs = (vlo ? 2 : 1) * n;           // float2 per stored vector
-        float2 *Vd = reinterpret_cast<float2 *>(w.V);   // (m+1) vectors
-        int rc = run(K_SCALE, 1, 16.0 * dn + vb * dn, 2.0 * dn,
-                     [&] { return dst_k_split_f64_df(n, r, w.nrm + rslot, Vd, s, vlo); });
-        if (rc) return rc;
-        Hess hs(m);
-        hs.start(rnorm);
-        // Every step of the cycle runs on the device (the second pass is gated
-        // there, norms and scaling too), so all steps are enqueued at once, each
-        // writing its own record in w.cols; the columns come back with one
-        // synchronisation per cycle.  Steps after the one that meets the
-        // tolerance (or breaks down) have run but are discarded.
-        const int steps = std::min(m, max_iters - iters);
-        if (steps < 1) return DST_OK;
+        const double vb = vlo ? 16.0 : 8.0;
+        const int64_t vs = (vlo ? 2 : 1) * n;
+        float2 *Vd = reinterpret_cast<float2 *>(w.V);
+        int rc;
         DST_CUDA_TRY(cudaMemsetAsync(w.cols, 0, sizeof(double) * COL_STRIDE * steps, s));
         prof.chain = true;          // only kernels are enqueued until the loop ends
         prof.last = -1;
@@ -545,9 +562,62 @@ struct Solver {
                 return rc;
         }
         prof.chain = false;
+        return DST_OK;
+    }
+
+    // Enqueue a cycle's steps; a full cycle (steps == m) is captured once as a
+    // CUDA graph and replayed afterwards: same launches, same arguments, one
+    // graph launch instead of ~6 m kernel launches.  Falls back to direct
+    // launches if capture is not possible.
+    int full_cycles = 0;     // full cycles enqueued so far (the first runs uncaptured)
+    int enqueue_cycle(int steps, bool full, bool vlo, bool &replayed) {
+        replayed = false;
+        // capture from the second full cycle on: by then every kernel of the
+        // cycle has been launched once (per-device attributes set outside capture)
+        if (full && graph.ok && !graph.exec && full_cycles > 0) {
+            int rc = graph.capture(*this, steps, vlo);
+            if (rc) return rc;
+        }
+        if (full) ++full_cycles;
+        if (full && graph.exec) {
+            DST_CUDA_TRY(cudaGraphLaunch(graph.exec, s));
+            graph.account(*this);
+            replayed = true;
+            return DST_OK;
+        }
+        return enqueue_steps(steps, vlo);
+    }
+
+    // One GMRES(m) cycle for the correction equation A d = r (d = 0 on entry),
+    // FP32 operator apply on a df32 basis with df32 Gram-Schmidt: V_0 = r/||r||
+    // (||r||^2 in w.nrm[rslot]), d += V y at the end (FP64).
+    // vlo = false: the basis is stored in FP32 (hi planes only, 8 B per entry)
+    // and the same compensated kernels run on it.
+    int cycle_df(double2 *d, const double2 *r, int rslot, double rnorm, double tol_abs, int max_iters, bool vlo) {
+        const int m = w.m;
+        const int64_t n = w.n;
+        const double dn = (double)n;
+        const double vb = vlo ? 16.0 : 8.0;             // bytes per stored basis entry
+        const int64_t vs = (vlo ? 2 : 1) * n;           // float2 per stored vector
+        float2 *Vd = reinterpret_cast<float2 *>(w.V);   // (m+1) vectors
+        int rc = run(K_SCALE, 1, 16.0 * dn + vb * dn, 2.0 * dn,
+                     [&] { return dst_k_split_f64_df(n, r, w.nrm + rslot, Vd, s, vlo); });
+        if (rc) return rc;
+        Hess hs(m);
+        hs.start(rnorm);
+        // Every step of the cycle runs on the device (the second pass is gated
+        // there, norms and scaling too), so all steps are enqueued at once, each
+        // writing its own record in w.cols; the columns come back with one
+        // synchronisation per cycle.  Steps after the one that meets the
+        // tolerance (or breaks down) have run but are discarded.
+        const int steps = std::min(m, max_iters - iters);
+        if (steps < 1) return DST_OK;
+        bool replayed = false;
+        if ((rc = enqueue_cycle(steps, steps == m, vlo, replayed))) return rc;
         DST_CUDA_TRY(cudaMemcpyAsync(w.host_cols, w.cols, sizeof(double) * COL_STRIDE * steps,
                                      cudaMemcpyDeviceToHost, s));
         if ((rc = sync())) return rc;
+        if (replayed) graph.harvest(prof);
         bool breakdown = false;
         int k = 0;
         for (int j = 0; j < steps; ++j) {
@@ -571,6 +641,87 @@ struct Solver {
         return DST_OK;
     }
 };
+
+// A private stream per thread for capturing (the caller's stream may be the
+// legacy default stream, which cannot be captured).
+static cudaStream_t capture_stream() {
+    static thread_local cudaStream_t cs = nullptr;
+    static thread_local int cs_dev = -1;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (!cs || cs_dev != dev) {
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            cs = nullptr;
+            return nullptr;
+        }
+        cs_dev = dev;
+    }
+    return cs;
+}
+
+int CycleGraph::capture(Solver &sv, int steps, bool vlo) {
+    cudaStream_t cs = capture_stream();
+    if (!cs) { ok = false; return DST_OK; }
+    // the accounting of the enqueue is taken as the per-replay amount, not counted now
+    Prof &p = sv.prof;
+    double l0[K_NCLASS], b0[K_NCLASS], f0[K_NCLASS];
+    for (int c = 0; c < K_NCLASS; ++c) { l0[c] = p.launches[c]; b0[c] = p.bytes[c]; f0[c] = p.flops[c]; }
+    const double tb0 = sv.bytes;
+    const size_t line0 = p.line.size(), pend0 = p.pending.size();
+    const int last0 = p.last;
+    cudaStream_t saved = sv.s;
+    sv.s = cs;
+    int rc = DST_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        sv.s = saved;
+        ok = false;
+        return DST_OK;
+    }
+    p.capturing = true;
+    rc = sv.enqueue_steps(steps, vlo);
+    p.capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    sv.s = saved;
+    cudaGraphExec_t ex = nullptr;
+    const bool good = rc == DST_OK && ec == cudaSuccess && g &&
+                      cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    // events recorded into the graph belong to it
+    for (size_t k = line0; k < p.line.size(); ++k) events.push_back(p.line[k]);
+    for (size_t k = pend0; k < p.pending.size(); ++k)
+        pending.push_back({p.pending[k].cls, p.pending[k].a - (int)line0, p.pending[k].b - (int)line0});
+    p.line.resize(line0);
+    p.pending.resize(pend0);
+    p.last = last0;
+    p.chain = false;
+    for (int c = 0; c < K_NCLASS; ++c) {
+        launches[c] = p.launches[c] - l0[c]; bytes[c] = p.bytes[c] - b0[c]; flops[c] = p.flops[c] - f0[c];
+        p.launches[c] = l0[c]; p.bytes[c] = b0[c]; p.flops[c] = f0[c];
+    }
+    total_bytes = sv.bytes - tb0;
+    sv.bytes = tb0;
+    if (!good) {
+        if (ex) cudaGraphExecDestroy(ex);
+        for (auto e : events) cudaEventDestroy(e);
+        events.clear();
+        pending.clear();
+        ok = false;
+        return DST_OK;
+    }
+    exec = ex;
+    return DST_OK;
+}
+
+void CycleGraph::account(Solver &sv) {
+    for (int c = 0; c < K_NCLASS; ++c) {
+        sv.prof.launches[c] += launches[c]; sv.prof.bytes[c] += bytes[c]; sv.prof.flops[c] += flops[c];
+    }
+    sv.bytes += total_bytes;
+}
 
 }  // namespace
 
