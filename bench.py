@@ -18,7 +18,7 @@ FP64 CPU oracle timed on the host cores, and the throughput of the batched
 solve (dst_solve_batch) on two seeded sets of independent 1+1 / 2+1 solves.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-       python bench.py --ncu-case solve60|apply32_zb|apply32_klein|apply64_klein  (ncu capture cases)
+       python bench.py --ncu-case solve60|solve60_klein32|apply32_zb|apply32_klein|apply64_klein  (ncu cases)
 N > 1 runs under torch.distributed.run: independent replicas, one per GPU.
 """
 
@@ -223,22 +223,27 @@ def time_apply(torch, B, mesh, prec, n, iters=40):
     return ms, 2.0 * n * esz / (ms * 1e-3) / 1e9
 
 
-NCU_CASES = ("solve60", "apply32_zb", "apply32_klein", "apply64_klein")
+NCU_CASES = ("solve60", "solve60_klein32", "apply32_zb", "apply32_klein", "apply64_klein")
 
 
 def run_ncu_case(case):
     """Small fixed launches for ncu captures (nothing timed, nothing printed as a bench line).
 
     solve60: the first 60 Arnoldi steps (two GMRES(30) cycles) of the bench's mixed solve;
+    solve60_klein32: the same on the 3+1 Klein workload at 32^3 x 32 (4.06M unknowns, large
+    enough for the bulk-copy fed projection);
     apply32_zb / apply32_klein / apply64_klein: 12 operator applies on the 96^2 x 96 bench
     mesh or the 48^3 x 48 3+1 Klein mesh, over rotating buffers.
     """
     import torch
     from paper_2103_14588_gb300 import binding as B
     torch.cuda.set_device(0)
-    w = W.klein_3p1(p0=1.05) if case.endswith("klein") else W.zb_2p1()
+    if case == "solve60_klein32":
+        w = W.klein_3p1(n=32, nt=32, p0=1.05)
+    else:
+        w = W.klein_3p1(p0=1.05) if case.endswith("klein") else W.zb_2p1()
     with B.Mesh.from_workload(w) as m:
-        if case == "solve60":
+        if case.startswith("solve60"):
             psi = torch.zeros(m.n_unknowns, dtype=torch.complex128, device="cuda")
             st = B.dst_solve(m.handle, {"restart": RESTART, "rtol": RTOL, "max_iters": 60, "mixed_precision": 1}, psi)
             torch.cuda.synchronize()

@@ -28,6 +28,7 @@
 // values; updated vectors are rounded to FP32 once.
 #include "blas.h"
 #include "df_arith.cuh"
+#include "tma.cuh"
 
 namespace dst {
 
@@ -366,6 +367,210 @@ project_f32_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
+// ---- FP32-stored basis, fed by bulk asynchronous copies --------------------
+//
+// The same projection as project_f32_kernel, but the basis and w reach shared
+// memory through a ring of TMA_SLOTS 16 KB bulk copies completed on mbarriers:
+// a producer warp keeps up to 96 KB per CTA in flight (two CTAs per SM),
+// independent of the arithmetic, in contiguous 16 KB transfers, refilling a
+// slot once all eight consumer warps have released it.  Each CTA owns a
+// contiguous slice of entries, cut into 2048-entry chunks; the copy sequence
+// is, per group of four basis vectors and per chunk, the chunk of w and then
+// the chunks of the group's vectors (w is read once per group: reducing every
+// vector's chunk contribution over the warp instead, to read w once, made the
+// consumers the bottleneck).  Each chunk's contribution is accumulated in the
+// anchored scheme with a bound taken from that chunk of w, then folded into a
+// df32 per-thread sum.
+constexpr int TMA_CHUNK = 2048;                 // entries per copy (16 KB)
+constexpr int TMA_SLOTS = 6;                    // ring: 6 x 16 KB (two CTAs per SM)
+constexpr int TMA_SMEM = TMA_SLOTS * TMA_CHUNK * 8;
+constexpr unsigned TMA_WAIT_LIMIT = 1u << 22;   // try_wait attempts before a wait is declared failed
+
+constexpr int TMA_THREADS = DF_THREADS + 32;   // eight consumer warps and one producer warp
+
+__global__ void __launch_bounds__(TMA_THREADS, 2)
+project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float2 *__restrict__ w,
+                   double2 *__restrict__ partials, const double *gate, double2 *__restrict__ h,
+                   double *__restrict__ wnrm2, unsigned *__restrict__ ticket, double *err) {
+    if (gate != nullptr && !(gate[0] < 0.5 * gate[3])) {           // DGKS: no second pass needed
+        if (blockIdx.x == 0)
+            for (int j = threadIdx.x; j < nvec; j += TMA_THREADS) h[j] = make_double2(0.0, 0.0);
+        return;
+    }
+    constexpr int NW = DF_THREADS / 32;              // consumer warps
+    constexpr int U = TMA_CHUNK / 2;                 // float4 units (two entries) per chunk
+    constexpr int UPT = U / DF_THREADS;              // units per consumer thread per chunk
+    extern __shared__ __align__(128) float4 ring[];  // TMA_SLOTS x U
+    __shared__ __align__(8) uint64_t full[TMA_SLOTS], empty[TMA_SLOTS];
+    __shared__ double red[NW][2 * DST_MAX_VEC + 1];
+    __shared__ int failed, s_issued, s_consumed;
+    volatile int *vfailed = &failed;                 // polled across warps
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int64_t b, e;
+    df_slice2(n, b, e);
+    const int64_t len = e > b ? e - b : 0;
+    const int nch = (int)((len + TMA_CHUNK - 1) / TMA_CHUNK);
+    const int ngr = (nvec + 3) / 4;
+    const int K = nch * (ngr + nvec);                // copies this CTA consumes
+    if (tid == 0) {
+        for (int q = 0; q < TMA_SLOTS; ++q) {
+            mbar_init(&full[q], 1);                  // the producer's arrival + the copy's bytes
+            mbar_init(&empty[q], NW);                // one arrival per consumer warp
+        }
+        failed = 0;
+        s_issued = 0;
+        s_consumed = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    DfAcc wn;
+    wn.zero();
+    if (warp == NW) {
+        // producer warp: lane 0 issues the copies in consumption order, refilling a
+        // slot once every consumer warp has released it
+        if (lane == 0) {
+            int pg = 0, pc = 0, pq = 0, k = 0;
+            for (; k < K && !*vfailed; ++k) {
+                const int slot = k % TMA_SLOTS;
+                if (k >= TMA_SLOTS &&
+                    !mbar_wait_bounded(&empty[slot], (unsigned)(((k / TMA_SLOTS) - 1) & 1), TMA_WAIT_LIMIT)) {
+                    *vfailed = 1;
+                    break;
+                }
+                const int gv = nvec - 4 * pg < 4 ? nvec - 4 * pg : 4;
+                const int64_t c0 = b + (int64_t)pc * TMA_CHUNK;
+                const int64_t cnt = e - c0 < TMA_CHUNK ? e - c0 : TMA_CHUNK;
+                const float2 *src = pq == 0 ? w + c0 : V + (int64_t)(4 * pg + pq - 1) * n + c0;
+                const unsigned bytes = (unsigned)(cnt * (int64_t)sizeof(float2));
+                mbar_arrive_expect_tx(&full[slot], bytes);
+                bulk_g2s(ring + (size_t)slot * U, src, bytes, &full[slot]);
+                if (++pq > gv) {
+                    pq = 0;
+                    if (++pc == nch) { pc = 0; ++pg; }
+                }
+            }
+            s_issued = k;
+        }
+    } else {
+        int k = 0;                                   // next copy to consume
+        auto wait_item = [&]() {
+            const int slot = k % TMA_SLOTS;
+            if (!*vfailed && !mbar_wait_bounded(&full[slot], (unsigned)((k / TMA_SLOTS) & 1), TMA_WAIT_LIMIT))
+                *vfailed = 1;
+            return (const float4 *)(ring + (size_t)slot * U);
+        };
+        auto release_item = [&]() {
+            __syncwarp();                            // the warp is done with slot k
+            if (lane == 0) mbar_arrive(&empty[k % TMA_SLOTS]);
+            ++k;
+        };
+        for (int g = 0; g < ngr && !*vfailed; ++g) {
+            const int gv = nvec - 4 * g < 4 ? nvec - 4 * g : 4;
+            DfAcc R[4], I[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { R[q].zero(); I[q].zero(); }
+            for (int c = 0; c < nch; ++c) {
+                const int64_t c0 = b + (int64_t)c * TMA_CHUNK;
+                const int units = (int)(((e - c0 < TMA_CHUNK) ? e - c0 : TMA_CHUNK) >> 1);
+                float4 a[UPT];
+                float bound = 0.f;
+                {
+                    const float4 *sw4 = wait_item();
+#pragma unroll
+                    for (int i = 0; i < UPT; ++i) {
+                        const int u = tid + i * DF_THREADS;
+                        a[i] = u < units ? sw4[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        bound += (fabsf(a[i].x) + fabsf(a[i].y)) + (fabsf(a[i].z) + fabsf(a[i].w));
+                        if (g == 0) {
+                            float p, r;
+                            p = a[i].x * a[i].x; r = fmaf(a[i].x, a[i].x, -p); wn.add(p, r);
+                            p = a[i].y * a[i].y; r = fmaf(a[i].y, a[i].y, -p); wn.add(p, r);
+                            p = a[i].z * a[i].z; r = fmaf(a[i].z, a[i].z, -p); wn.add(p, r);
+                            p = a[i].w * a[i].w; r = fmaf(a[i].w, a[i].w, -p); wn.add(p, r);
+                        }
+                    }
+                    release_item();
+                }
+                const float sigma = anchor_above(bound);
+                for (int q = 0; q < gv; ++q) {
+                    const float4 *sv = wait_item();
+                    AnAcc re, im;
+                    re.init(sigma);
+                    im.init(sigma);
+#pragma unroll
+                    for (int i = 0; i < UPT; ++i) {
+                        const int u = tid + i * DF_THREADS;
+                        if (u < units) {
+                            const float4 v = sv[u];
+                            cdot_an(v.x, v.y, a[i].x, a[i].y, re, im);
+                            cdot_an(v.z, v.w, a[i].z, a[i].w, re, im);
+                        }
+                    }
+                    df_add(R[q].hi, R[q].lo, re.hi - sigma, re.lo);
+                    df_add(I[q].hi, I[q].lo, im.hi - sigma, im.lo);
+                    release_item();
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q < gv) {
+                    const double sr = dfwarp_sum(R[q]), si = dfwarp_sum(I[q]);
+                    if (lane == 0) { red[warp][2 * (4 * g + q)] = sr; red[warp][2 * (4 * g + q) + 1] = si; }
+                }
+            }
+        }
+        if (tid == 0) s_consumed = k;
+    }
+    __syncthreads();
+    // a failed wait can leave copies in flight: wait for them (bounded) before exit
+    if (tid == 0 && *vfailed)
+        for (int q = s_consumed; q < s_issued; ++q)
+            mbar_wait_bounded(&full[q % TMA_SLOTS], (unsigned)((q / TMA_SLOTS) & 1), 1024);
+    // every issued copy was waited for by the consumers (or the producer stopped
+    // issuing after a failed wait); the ring is idle here
+    const double wsum = warp < NW ? dfwarp_sum(wn) : 0.0;
+    if (lane == 0 && warp < NW) red[warp][2 * DST_MAX_VEC] = wsum;
+    __syncthreads();
+    if (*vfailed && tid == 0 && err) *err = 1.0;
+    for (int q = tid; q < 2 * nvec; q += TMA_THREADS) {
+        double s_ = 0.0;
+#pragma unroll
+        for (int kk = 0; kk < NW; ++kk) s_ += red[kk][q];
+        reinterpret_cast<double *>(partials + (int64_t)blockIdx.x * nvec)[q] = s_;
+    }
+    // ||w||^2 partial of this CTA goes after the coefficient partials of all CTAs
+    double *wparts = reinterpret_cast<double *>(partials + (int64_t)gridDim.x * nvec);
+    if (tid == 0) {
+        double s_ = 0.0;
+#pragma unroll
+        for (int kk = 0; kk < NW; ++kk) s_ += red[kk][2 * DST_MAX_VEC];
+        wparts[blockIdx.x] = s_;
+    }
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const double *pd = reinterpret_cast<const double *>(partials);
+    for (int q = warp; q < 2 * nvec + 1; q += NW) {
+        double s_ = 0.0;
+        if (q < 2 * nvec) {
+            for (unsigned kk = lane; kk < gridDim.x; kk += 32) s_ += __ldcg(pd + (size_t)kk * 2 * nvec + q);
+        } else if (wnrm2) {
+            for (unsigned kk = lane; kk < gridDim.x; kk += 32) s_ += __ldcg(wparts + kk);
+        }
+        s_ = dwarp_sum(s_);
+        if (lane == 0) {
+            if (q < 2 * nvec) reinterpret_cast<double *>(h)[q] = s_;
+            else if (wnrm2) *wnrm2 = s_;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) *ticket = 0u;
+}
+
 // w <- w - sum_j V_j h_j for an FP32-stored unit-norm basis and FP32 w (h in
 // FP64, split per CTA), rounded to FP32 once; partials of ||w||^2 of the
 // stored result.  Per entry the bound is |w component| + sum_j |h_j|_1.
@@ -574,6 +779,27 @@ int dst_k_project_df(int64_t n, int nvec, const float2 *V, const float2 *w, bool
         project_df_kernel<true><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wp, gate, h, wnrm2, ticket);
     else
         project_df_kernel<false><<<nblk, DF_THREADS, 0, s>>>(n, nvec, V, w, partials, wp, gate, h, wnrm2, ticket);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_tma_projection_blocks(int64_t n) {
+    int64_t b = (n + 2047) / 2048;
+    if (b > 2 * 152) b = 2 * 152;
+    return (int)(b < 1 ? 1 : b);
+}
+
+int dst_k_project_tma(int64_t n, int nvec, const float2 *V, const float2 *w, double2 *h, double2 *partials, int nblk,
+                      cudaStream_t s, double *wnrm2, const double *gate, unsigned *ticket, double *err) {
+    if (n & 1) return DST_ERR_ARG;
+    static bool configured[64] = {};
+    int dev = 0;
+    DST_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        DST_CUDA_TRY(cudaFuncSetAttribute(project_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM));
+        if (dev >= 0 && dev < 64) configured[dev] = true;
+    }
+    project_tma_kernel<<<nblk, TMA_THREADS, TMA_SMEM, s>>>(n, nvec, V, w, partials, gate, h, wnrm2, ticket, err);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
