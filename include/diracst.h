@@ -253,6 +253,30 @@ DST_API int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, dst
               void *stream);
 
 /*
+ * Tile-shape autotuner of the operator apply (no counterpart in the paper:
+ * a GPU launch-configuration choice; every shape computes each output from
+ * the same neighbours in the same order, so FP64 applies agree bit for bit and
+ * FP32 applies to rounding.  The autotuner picks by timing, so a mixed-precision
+ * solve is reproducible bit for bit only with a fixed shape: set one with
+ * dst_set_apply_variant before the first solve).  1+1 and
+ * 2+1 meshes have 3 shapes (0 = the default: 1+1 tiles of 256 nodes x 32
+ * time layers, then 128 x 16 and 64 x 8; 2+1 tiles of 32 x 8 nodes x 8 layers,
+ * then 32 x 8 x 4 and 16 x 8 x 8); 3+1 meshes have one.  dst_solve runs the
+ * autotuner on a mesh's first solve (in its own workspace).
+ *
+ * dst_tune_apply: times every shape of both precisions on the mesh (3 applies
+ * each after a warm-up, on a stream-ordered scratch of 32 bytes per unknown)
+ * and keeps the fastest; synchronises `stream`.  DST_ERR_ARG / OOM / CUDA.
+ * dst_set_apply_variant: use shape `variant` (0 .. count-1) for `precision`
+ * (DST_FP64 / DST_FP32) from now on; marks the mesh tuned.  DST_ERR_ARG for a
+ * bad precision or variant.
+ * dst_get_apply_variant: the current shape and the number of shapes.
+ */
+DST_API int dst_tune_apply(dst_mesh *mesh, void *stream);
+DST_API int dst_set_apply_variant(dst_mesh *mesh, int precision, int variant);
+DST_API int dst_get_apply_variant(const dst_mesh *mesh, int precision, int *variant, int *count);
+
+/*
  * Batched solve: Algorithm 1 step 6 for `count` independent meshes at once,
  * each psi[i] (DEVICE, complex FP64, meshes[i]'s n_unknowns, 16-byte aligned)
  * receiving the solution of its own mesh.  Every mesh must be 1+1 or 2+1, live

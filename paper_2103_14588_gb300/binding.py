@@ -26,6 +26,7 @@ EXPORTED = (
     "dst_set_initial_data", "dst_build_rhs", "dst_apply_operator", "dst_arnoldi_project",
     "dst_arnoldi_update", "dst_default_solve_opts", "dst_solve", "dst_status_string",
     "dst_last_error_detail", "dst_arnoldi_project_noalloc", "dst_observables", "dst_solve_batch",
+    "dst_tune_apply", "dst_set_apply_variant", "dst_get_apply_variant",
 )
 
 
@@ -88,6 +89,9 @@ def _load():
         "dst_default_solve_opts": (c_int, [P(dst_solve_opts)]),
         "dst_solve": (c_int, [vp, P(dst_solve_opts), vp, P(dst_solve_stats), vp]),
         "dst_solve_batch": (c_int, [c_int, P(vp), P(dst_solve_opts), P(vp), P(dst_solve_stats), vp]),
+        "dst_tune_apply": (c_int, [vp, vp]),
+        "dst_set_apply_variant": (c_int, [vp, c_int, c_int]),
+        "dst_get_apply_variant": (c_int, [vp, c_int, P(c_int), P(c_int)]),
         "dst_status_string": (ctypes.c_char_p, [c_int]),
         "dst_last_error_detail": (ctypes.c_char_p, []),
     }
@@ -275,6 +279,22 @@ def dst_solve(mesh, opts, psi, stream=None):
     rc = _lib.dst_solve(mesh, ctypes.byref(o), p, ctypes.byref(st), _stream(stream, psi))
     _check(rc, "dst_solve")
     return st.as_dict()
+
+
+def dst_tune_apply(mesh, stream=0):
+    """Run the apply tile-shape autotuner on the mesh (both precisions)."""
+    _check(_lib.dst_tune_apply(mesh, stream if isinstance(stream, int) else stream.cuda_stream), "dst_tune_apply")
+
+
+def dst_set_apply_variant(mesh, precision, variant):
+    _check(_lib.dst_set_apply_variant(mesh, precision, variant), "dst_set_apply_variant")
+
+
+def dst_get_apply_variant(mesh, precision):
+    """(current tile shape, number of shapes) for the precision."""
+    v, c = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.dst_get_apply_variant(mesh, precision, ctypes.byref(v), ctypes.byref(c)), "dst_get_apply_variant")
+    return v.value, c.value
 
 
 def dst_solve_batch(meshes, opts, psis, stream=None):

@@ -24,14 +24,20 @@ namespace dst {
 // Output tile TX x TY x TZ per CTA and TT time layers; each thread computes RY
 // consecutive y outputs (2+1: the x stencils of the rows they share are
 // computed once).
-template <int D> struct PipeTile;
-template <> struct PipeTile<1> { static constexpr int TX = 256, TY = 1, TZ = 1, TT = 32, RY = 1; };
-template <> struct PipeTile<2> { static constexpr int TX = 32, TY = 8, TZ = 1, TT = 8, RY = 2; };
-template <> struct PipeTile<3> { static constexpr int TX = 16, TY = 4, TZ = 4, TT = 8, RY = 1; };
+// TV selects one of the tile shapes the autotuner chooses from (variant 0 is
+// the default): smaller tiles and time chunks give small meshes more CTAs.
+template <int D, int TV = 0> struct PipeTile;
+template <> struct PipeTile<1, 0> { static constexpr int TX = 256, TY = 1, TZ = 1, TT = 32, RY = 1; };
+template <> struct PipeTile<1, 1> { static constexpr int TX = 128, TY = 1, TZ = 1, TT = 16, RY = 1; };
+template <> struct PipeTile<1, 2> { static constexpr int TX = 64, TY = 1, TZ = 1, TT = 8, RY = 1; };
+template <> struct PipeTile<2, 0> { static constexpr int TX = 32, TY = 8, TZ = 1, TT = 8, RY = 2; };
+template <> struct PipeTile<2, 1> { static constexpr int TX = 32, TY = 8, TZ = 1, TT = 4, RY = 2; };
+template <> struct PipeTile<2, 2> { static constexpr int TX = 16, TY = 8, TZ = 1, TT = 8, RY = 2; };
+template <> struct PipeTile<3, 0> { static constexpr int TX = 16, TY = 4, TZ = 4, TT = 8, RY = 1; };
 
-template <int D, int NC, typename T>
+template <int D, int NC, typename T, int TV = 0>
 struct PipeShape {
-    using Tile = PipeTile<D>;
+    using Tile = PipeTile<D, TV>;
     static constexpr int BX = Tile::TX + 2;
     static constexpr int BY = D >= 2 ? Tile::TY + 2 : 1;
     static constexpr int BZ = D >= 3 ? Tile::TZ + 2 : 1;
@@ -78,22 +84,22 @@ __device__ __forceinline__ void cp_async_wait_n(int n) {
 // within a time layer (-1: outside a non-periodic boundary, zero-filled) and
 // destination byte offset within a ring slot.  Computed once per thread, so
 // the plane loop does no index arithmetic (periodic wrap needs 64-bit modulo).
-template <int D, int NC, typename T>
+template <int D, int NC, typename T, int TV>
 struct CopyPlan {
     static constexpr int PER_THREAD =
-        (PipeShape<D, NC, T>::BOX * PipeShape<D, NC, T>::CHUNKS + PipeShape<D, NC, T>::NTHR - 1) /
-        PipeShape<D, NC, T>::NTHR;
+        (PipeShape<D, NC, T, TV>::BOX * PipeShape<D, NC, T, TV>::CHUNKS + PipeShape<D, NC, T, TV>::NTHR - 1) /
+        PipeShape<D, NC, T, TV>::NTHR;
     int src[PER_THREAD];
     int dst[PER_THREAD];
 };
 
-template <int D, int NC, typename T>
+template <int D, int NC, typename T, int TV>
 __device__ __forceinline__ void make_copy_plan(const OpParams &p, int64_t x0, int64_t y0, int64_t z0,
-                                               CopyPlan<D, NC, T> &cp) {
-    using S = PipeShape<D, NC, T>;
+                                               CopyPlan<D, NC, T, TV> &cp) {
+    using S = PipeShape<D, NC, T, TV>;
     const int64_t nx = p.ax[0].n, ny = p.ax[1].n;
 #pragma unroll
-    for (int j = 0; j < CopyPlan<D, NC, T>::PER_THREAD; ++j) {
+    for (int j = 0; j < CopyPlan<D, NC, T, TV>::PER_THREAD; ++j) {
         const int i = threadIdx.x + j * S::NTHR;
         cp.dst[j] = -1;
         cp.src[j] = -1;
@@ -109,10 +115,10 @@ __device__ __forceinline__ void make_copy_plan(const OpParams &p, int64_t x0, in
 }
 
 // Issue the copies of one plane (tile box, one-node halo) into a ring slot.
-template <int D, int NC, typename T>
-__device__ __forceinline__ void issue_plane(const CopyPlan<D, NC, T> &cp, const char *layer, char *slot) {
+template <int D, int NC, typename T, int TV>
+__device__ __forceinline__ void issue_plane(const CopyPlan<D, NC, T, TV> &cp, const char *layer, char *slot) {
 #pragma unroll
-    for (int j = 0; j < CopyPlan<D, NC, T>::PER_THREAD; ++j)
+    for (int j = 0; j < CopyPlan<D, NC, T, TV>::PER_THREAD; ++j)
         if (cp.dst[j] >= 0) cp_async16(slot + cp.dst[j], layer + (cp.src[j] >= 0 ? cp.src[j] : 0), cp.src[j] >= 0);
 }
 
@@ -305,12 +311,12 @@ __device__ __forceinline__ void fields_std_rows(Get get, const StdConst<T> &sc, 
 // `ring` (PipeShape::SMEM bytes of shared memory), PipeShape::NTHR threads.
 // Ends with every copy complete; a caller that reuses the ring for another
 // tile synchronises the CTA first.
-template <int D, int NC, typename T, bool NOV, bool STD>
+template <int D, int NC, typename T, bool NOV, bool STD, int TV = 0>
 __device__ __forceinline__ void apply_pipe_tile(const OpParams &p, const typename C2<T>::type *__restrict__ x,
                                                 typename C2<T>::type *__restrict__ y, int64_t tiles_x,
                                                 int64_t tiles_y, int64_t tile, int64_t chunk, char *ring) {
     using V = typename C2<T>::type;
-    using S = PipeShape<D, NC, T>;
+    using S = PipeShape<D, NC, T, TV>;
     using Tile = typename S::Tile;
     constexpr int RY = Tile::RY;
     constexpr int TYT = Tile::TY / RY;                  // threads along y
@@ -361,8 +367,8 @@ __device__ __forceinline__ void apply_pipe_tile(const OpParams &p, const typenam
         const T wl = valid[0] ? k.wl[sb] : (T)0, wr = valid[0] ? k.wr[sb] : (T)0;
         wxs[sb][0] = wl; wxs[sb][1] = 2 * (wl + wr); wxs[sb][2] = wr;
     }
-    CopyPlan<D, NC, T> cplan;
-    make_copy_plan<D, NC, T>(p, x0, y0, z0, cplan);
+    CopyPlan<D, NC, T, TV> cplan;
+    make_copy_plan<D, NC, T, TV>(p, x0, y0, z0, cplan);
     const T h6 = (T)(p.ht / 6.0);
     const int NY = D >= 2 ? 3 : 1;
     const int c0 = (tz * S::BY + ty) * S::BX + tx;      // box index of the (-1,-1,-1) neighbour of row 0
@@ -382,7 +388,7 @@ __device__ __forceinline__ void apply_pipe_tile(const OpParams &p, const typenam
     const char *issue_src = xsrc;
 
     auto issue_next = [&](int i) {      // plane i into the next ring slot (i strictly increasing)
-        if (i >= i_lo && i <= i_hi) issue_plane<D, NC, T>(cplan, issue_src, ring + (size_t)issue_slot * slot_bytes);
+        if (i >= i_lo && i <= i_hi) issue_plane<D, NC, T, TV>(cplan, issue_src, ring + (size_t)issue_slot * slot_bytes);
         cp_async_commit();
         issue_src += plane_bytes;
         issue_slot = issue_slot + 1 == S::STAGES ? 0 : issue_slot + 1;
@@ -518,19 +524,19 @@ __device__ __forceinline__ void apply_pipe_tile(const OpParams &p, const typenam
     (void)any_valid;
 }
 
-template <int D, int NC, typename T, bool NOV, bool STD>
-__global__ void __launch_bounds__(PipeShape<D, NC, T>::NTHR,
+template <int D, int NC, typename T, bool NOV, bool STD, int TV>
+__global__ void __launch_bounds__(PipeShape<D, NC, T, TV>::NTHR,
                                   sizeof(T) == 8 ? 1 : (D == 3 ? (STD ? 2 : 1) : 3))
 apply_pipe_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typename C2<T>::type *__restrict__ y,
                   int64_t tiles_x, int64_t tiles_y) {
     extern __shared__ __align__(16) char ring[];
-    apply_pipe_tile<D, NC, T, NOV, STD>(p, x, y, tiles_x, tiles_y, blockIdx.x, blockIdx.y, ring);
+    apply_pipe_tile<D, NC, T, NOV, STD, TV>(p, x, y, tiles_x, tiles_y, blockIdx.x, blockIdx.y, ring);
 }
 
-template <int D, int NC, typename T>
-int launch_apply_pipe(const OpParams &p, const typename C2<T>::type *x, typename C2<T>::type *y, cudaStream_t s) {
-    using S = PipeShape<D, NC, T>;
-    using Tile = PipeTile<D>;
+template <int D, int NC, typename T, int TV>
+int launch_apply_pipe_v(const OpParams &p, const typename C2<T>::type *x, typename C2<T>::type *y, cudaStream_t s) {
+    using S = PipeShape<D, NC, T, TV>;
+    using Tile = PipeTile<D, TV>;
     const int64_t tx = (p.ax[0].n + Tile::TX - 1) / Tile::TX;
     const int64_t ty = (p.ax[1].n + Tile::TY - 1) / Tile::TY;
     const int64_t tz = (p.ax[2].n + Tile::TZ - 1) / Tile::TZ;
@@ -548,10 +554,10 @@ int launch_apply_pipe(const OpParams &p, const typename C2<T>::type *x, typename
     bool all_std = true;        // no open axis: every node has the standard stencils
     for (int k = 0; k < D; ++k) all_std = all_std && p.ax[k].bc != DST_BC_OPEN;
     const int var = nov + 2 * (all_std ? 1 : 0);
-    auto kern = var == 0   ? apply_pipe_kernel<D, NC, T, false, false>
-                : var == 1 ? apply_pipe_kernel<D, NC, T, true, false>
-                : var == 2 ? apply_pipe_kernel<D, NC, T, false, true>
-                           : apply_pipe_kernel<D, NC, T, true, true>;
+    auto kern = var == 0   ? apply_pipe_kernel<D, NC, T, false, false, TV>
+                : var == 1 ? apply_pipe_kernel<D, NC, T, true, false, TV>
+                : var == 2 ? apply_pipe_kernel<D, NC, T, false, true, TV>
+                           : apply_pipe_kernel<D, NC, T, true, true, TV>;
     if (dev < 0 || dev >= DST_MAX_DEVICES_APPLY || !configured[var][dev]) {
         DST_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
         if (dev >= 0 && dev < DST_MAX_DEVICES_APPLY) configured[var][dev] = true;
@@ -559,6 +565,21 @@ int launch_apply_pipe(const OpParams &p, const typename C2<T>::type *x, typename
     kern<<<grid, S::NTHR, S::SMEM, s>>>(p, x, y, tx, ty);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
+}
+
+// Number of tile variants per spatial dimension.
+constexpr int pipe_tile_variants(int d) { return d == 3 ? 1 : 3; }
+
+// Launch with the tile variant the parameters carry for this precision.
+template <int D, int NC, typename T>
+int launch_apply_pipe(const OpParams &p, const typename C2<T>::type *x, typename C2<T>::type *y, cudaStream_t s) {
+    const int tv = p.tile_variant[sizeof(T) == 4 ? DST_FP32 : DST_FP64];
+    if (D == 3 || tv <= 0) return launch_apply_pipe_v<D, NC, T, 0>(p, x, y, s);
+    if constexpr (D < 3) {
+        if (tv == 1) return launch_apply_pipe_v<D, NC, T, 1>(p, x, y, s);
+        return launch_apply_pipe_v<D, NC, T, 2>(p, x, y, s);
+    }
+    return DST_ERR_ARG;
 }
 
 }  // namespace dst

@@ -784,6 +784,9 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     }
     sv.w.host = pinned;
     sv.w.host_cols = pinned + 8 * DST_MAX_VEC + 16;
+    // first solve on this mesh: pick the apply tile shapes (the basis storage,
+    // (m + 1) x 16 n bytes, is free scratch at this point)
+    if (!mesh->tuned && (rc = dst_internal_tune(mesh, sv.w.V, s))) return rc;
     const int64_t n = mesh->n_unknowns;
     // b = -D_w21 psi0 and ||b||
     sv.prof.on = o.profile != 0;

@@ -38,6 +38,7 @@ struct OpParams {
     int vmode;               // 0: x-only weights, 1: general per-element V, 2: no potential
     const double *wx;        // separable: [2*nel_x]: (m + V_ex) then (-m + V_ex)
     const double *Vel;       // general: V per spatial element (x fastest)
+    int tile_variant[2];     // apply tile shape per precision (index DST_FP64 / DST_FP32)
 };
 
 struct dst_mesh {
@@ -57,6 +58,8 @@ struct dst_mesh {
     double *d_V;                  // general potential (or null)
     std::vector<double> psi0;     // host copy of the initial layer
     double2 *d_psi0;              // device copy (null until set)
+    int tile_variant[2];          // apply tile shape per precision, set by the autotuner
+    bool tuned;                   // the autotuner has run on this mesh
     // GMRES workspace (allocated lazily by dst_solve)
     void *ws;
     size_t ws_bytes;
@@ -76,3 +79,8 @@ int dst_launch_rhs_d3(const OpParams &p, const double2 *psi0, double2 *b, cudaSt
 // Dispatch on the mesh dimension.
 int dst_internal_apply(const dst_mesh *mesh, int precision, const void *x, void *y, cudaStream_t s);
 int dst_internal_rhs(const dst_mesh *mesh, double2 *b, cudaStream_t s);
+// Time every apply tile variant of both precisions on scratch (at least
+// 32 * n_unknowns bytes of device memory, contents overwritten) and keep the
+// fastest in mesh->tile_variant; synchronises s.
+int dst_internal_tune(dst_mesh *mesh, void *scratch, cudaStream_t s);
+int dst_internal_tile_variants(const dst_mesh *mesh);

@@ -48,7 +48,79 @@ OpParams dst_internal_params(const dst_mesh *mesh) {
     p.vmode = mesh->v_general ? 1 : (mesh->V.empty() ? 2 : 0);
     p.wx = mesh->d_wx;
     p.Vel = mesh->d_V;
+    p.tile_variant[DST_FP64] = mesh->tile_variant[DST_FP64];
+    p.tile_variant[DST_FP32] = mesh->tile_variant[DST_FP32];
     return p;
+}
+
+int dst_internal_tile_variants(const dst_mesh *mesh) { return mesh->d == 3 ? 1 : 3; }
+
+int dst_internal_tune(dst_mesh *mesh, void *scratch, cudaStream_t s) {
+    const int nv = dst_internal_tile_variants(mesh);
+    mesh->tuned = true;
+    if (nv <= 1 || mesh->v_general) return DST_OK;     // one shape only / the general-potential kernel
+    const int64_t n = mesh->n_unknowns;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DST_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return DST_ERR_CUDA;
+    }
+    int rc = DST_OK;
+    for (int prec = 0; prec < 2 && rc == DST_OK; ++prec) {
+        const size_t esz = prec == DST_FP64 ? 16 : 8;
+        char *x = static_cast<char *>(scratch), *y = x + esz * n;
+        if (cudaMemsetAsync(x, 0, esz * n, s) != cudaSuccess) { rc = DST_ERR_CUDA; break; }
+        float best = 0.f;
+        int best_v = 0;
+        for (int v = 0; v < nv && rc == DST_OK; ++v) {
+            mesh->tile_variant[prec] = v;
+            rc = dst_internal_apply(mesh, prec, x, y, s);            // warm-up (and kernel attributes)
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3 && rc == DST_OK; ++r) rc = dst_internal_apply(mesh, prec, x, y, s);
+            cudaEventRecord(e1, s);
+            if (rc == DST_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = DST_ERR_CUDA;
+            float t = 0.f;
+            if (rc == DST_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = DST_ERR_CUDA;
+            if (rc == DST_OK && (v == 0 || t < best)) { best = t; best_v = v; }
+        }
+        mesh->tile_variant[prec] = best_v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+extern "C" int dst_tune_apply(dst_mesh *mesh, void *stream) {
+    if (!mesh) return DST_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *scratch = nullptr;
+    if (cudaMallocAsync(&scratch, (size_t)32 * mesh->n_unknowns, s) != cudaSuccess) {
+        cudaGetLastError();
+        return DST_ERR_OOM;
+    }
+    const int rc = dst_internal_tune(mesh, scratch, s);
+    cudaFreeAsync(scratch, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (rc != DST_OK) return rc;
+    DST_CUDA_TRY(e);
+    return DST_OK;
+}
+
+extern "C" int dst_set_apply_variant(dst_mesh *mesh, int precision, int variant) {
+    if (!mesh || (precision != DST_FP64 && precision != DST_FP32) || variant < 0 ||
+        variant >= dst_internal_tile_variants(mesh))
+        return DST_ERR_ARG;
+    mesh->tile_variant[precision] = variant;
+    mesh->tuned = true;
+    return DST_OK;
+}
+
+extern "C" int dst_get_apply_variant(const dst_mesh *mesh, int precision, int *variant, int *count) {
+    if (!mesh || (precision != DST_FP64 && precision != DST_FP32)) return DST_ERR_ARG;
+    if (variant) *variant = mesh->tile_variant[precision];
+    if (count) *count = dst_internal_tile_variants(mesh);
+    return DST_OK;
 }
 
 // Separable weights (m*beta + V_ex) per x element for beta = +1 and -1.  Only
@@ -116,6 +188,8 @@ extern "C" int dst_create_mesh(int d, const int64_t n_el[4], const double lo[4],
     m->d_V = nullptr;
     m->d_psi0 = nullptr;
     m->ws = nullptr;
+    m->tile_variant[0] = m->tile_variant[1] = 0;
+    m->tuned = false;
     m->ws_bytes = 0;
     if (cudaMalloc(&m->d_wx, sizeof(double) * 2 * m->nel[0]) != cudaSuccess) {
         delete m;
