@@ -561,7 +561,6 @@ extern "C" int dst_solve_batch(int count, dst_mesh *const *meshes, const dst_sol
             b.x = static_cast<double2 *>(psi[small[k]]);
             rc = dst_internal_rhs(mh, const_cast<double2 *>(b.b), s);
             packed.push_back(b);
-            small[k] = small[k];
         }
         // small[order[q]] is the mesh of packed[q]
         std::vector<int> mesh_of(cs_);

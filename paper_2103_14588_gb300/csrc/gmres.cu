@@ -611,7 +611,6 @@ struct Solver {
         const int64_t n = w.n;
         const double dn = (double)n;
         const double vb = vlo ? 16.0 : 8.0;             // bytes per stored basis entry
-        const int64_t vs = (vlo ? 2 : 1) * n;           // float2 per stored vector
         float2 *Vd = reinterpret_cast<float2 *>(w.V);   // (m+1) vectors
         int rc = run(K_SCALE, 1, 16.0 * dn + vb * dn, 2.0 * dn,
                      [&] { return dst_k_split_f64_df(n, r, w.nrm + rslot, Vd, s, vlo); });

@@ -54,3 +54,24 @@ def test_sommerfeld_potential_and_packet():
     assert w.psi0.shape == (1, 1, 63, 2)
     dens = np.sum(np.abs(w.psi0) ** 2, axis=-1).ravel()
     assert dens[0] < 1e-6 * dens.max() and dens[-1] < 1e-20 * dens.max()
+
+
+def test_batch_instances_draws():
+    """The batched-solve instance set is a pure function of the seed, and its draws
+    stay in the stated ranges (dimension, element counts, mass, momentum, barrier)."""
+    a = W.batch_instances(40, 4)
+    b = W.batch_instances(40, 4)
+    c = W.batch_instances(40, 5)
+    assert [w.name for w in a] == [w.name for w in b]
+    assert any(x.name != y.name for x, y in zip(a, c))
+    assert {w.d for w in a} == {1, 2}
+    for w in a:
+        lo, hi = (32, 256) if w.d == 1 else (16, 48)
+        axes = [w.n_el[0], w.n_el[3]] + ([w.n_el[1]] if w.d == 2 else [])
+        assert all(lo <= k <= hi for k in axes)
+        assert 0.5 <= w.m <= 2.0 and -4.0 <= w.extra["p0"] <= 4.0 and 0.0 <= w.extra["V0"] <= 3.0
+        assert w.V.shape == (w.n_el[0] * (w.n_el[1] if w.d == 2 else 1),)
+        assert np.all(w.V[: w.n_el[0] // 2 - 1] == 0.0) and np.all(w.V[w.n_el[0] // 2 + 1: w.n_el[0]] == w.extra["V0"])
+        dens = np.sum(np.abs(w.psi0) ** 2)
+        h = np.prod([(w.hi[k] - w.lo[k]) / w.n_el[k] for k in range(w.d)])
+        assert abs(dens * h - 1.0) < 1e-12
