@@ -4,9 +4,9 @@
 One step = one whole solve of the 2+1 Zitterbewegung workload (96 x 96 space
 x 96 time Q1 elements, 2-component spinor, 1,769,472 complex unknowns) to
 relative residual 1e-8: right-hand side, FP32 operator applies inside GMRES(30),
-classical Gram-Schmidt with a selective second pass on an FP32-stored Krylov
-basis in compensated (FP64-class) arithmetic, FP64 Givens/least squares, FP64
-residuals and iterative refinement.
+one classical Gram-Schmidt pass per step (PETSc's GMRES default) on an
+FP32-stored Krylov basis in compensated arithmetic, FP64 Givens/least squares,
+FP64 residuals and iterative refinement.
 Inputs are resident in HBM when the timed region starts; the GMRES basis
 (31 x 28 MB) exceeds L2, so no L2 flush is needed between steps.
 

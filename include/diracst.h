@@ -185,9 +185,10 @@ typedef struct {
     int profile;            /* 1: time every kernel class with CUDA events (small overhead) */
     int inner_cycles;       /* GMRES(m) cycles per refinement step (mixed only; 0 = until
                                inner_rtol), default 1 */
-    int ortho;              /* Gram-Schmidt: 0 = classical, second pass only when the DGKS test
+    int ortho;              /* Gram-Schmidt (default 2): 0 = classical, second pass only when the DGKS test
                                asks (norm fell below 1/sqrt 2 of its value before the pass);
-                               1 = always two classical passes (CGS2) */
+                               1 = always two classical passes (CGS2); 2 = one classical pass,
+                               never reorthogonalised (PETSc's default for GMRES) */
     int mixed_ortho;        /* mixed only: arithmetic of the inner Gram-Schmidt (default 2).  0 = double-FP32
                                (basis stored as FP32 hi/lo planes, 48-bit significand, error-free
                                FP32 products and sums, FP64 reductions; needs inner_cycles = 1),
@@ -236,9 +237,9 @@ typedef struct {
 
 /* Fill opts with the defaults (restart 30, max_iters 100000, rtol 1e-8,
  * FP64, inner_rtol 1e-4, max_refine 100000, zero initial guess, no
- * profiling, one inner cycle per refinement, selective reorthogonalisation,
- * inner Gram-Schmidt on an FP32-stored basis in compensated arithmetic,
- * GMRES). */
+ * profiling, one inner cycle per refinement, one classical Gram-Schmidt pass
+ * without reorthogonalisation, inner Gram-Schmidt on an FP32-stored basis in
+ * compensated arithmetic, GMRES). */
 DST_API int dst_default_solve_opts(dst_solve_opts *opts);
 
 /*

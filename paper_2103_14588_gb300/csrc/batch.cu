@@ -316,7 +316,7 @@ batch_solve_kernel(const BatchInst *__restrict__ insts, BatchOpts o) {
                 __shared__ double2 col[BMAXV];
                 if (tid < nv) col[tid] = hcol[tid];
                 __syncthreads();
-                if (o.ortho == 1 || after < 0.5 * before) {
+                if (o.ortho == 1 || (o.ortho == 0 && after < 0.5 * before)) {
                     project(wv, nv);
                     after = update(wv, nv);
                     if (tid < nv) col[tid] = zadd(col[tid], hcol[tid]);
@@ -451,7 +451,7 @@ extern "C" int dst_solve_batch(int count, dst_mesh *const *meshes, const dst_sol
     if (count <= 0 || !meshes || !opts || !psi || !stats) return DST_ERR_ARG;
     const dst_solve_opts &u = *opts;
     if (u.restart < 1 || u.restart > BMAXM || u.max_iters < 1 || u.max_refine < 1 || !(u.rtol > 0) ||
-        !(u.inner_rtol > 0) || u.ortho < 0 || u.ortho > 1 || u.method != 0)
+        !(u.inner_rtol > 0) || u.ortho < 0 || u.ortho > 2 || u.method != 0)
         return DST_ERR_ARG;
     int dev = 0;
     DST_CUDA_TRY(cudaGetDevice(&dev));

@@ -252,7 +252,7 @@ struct Solver {
     int iters = 0;
     int restarts = 0;
     int reorths = 0;
-    int ortho = 0;           // 0: DGKS selective second pass, 1: always two passes
+    int ortho = 0;           // 0: DGKS selective second pass, 1: always two passes, 2: one pass
     double resid_est = 0.0;
     Prof prof;
     CycleGraph graph;
@@ -410,6 +410,7 @@ struct Solver {
     // the residual (beta_out = -1).
     int gmres(int prec, double2 *x, const double2 *rhs, bool x_zero, double tol_abs, int max_iters,
               double &beta_out, int max_cycles = 0x7fffffff) {
+        if (ortho == 2) DST_CUDA_TRY(cudaMemsetAsync(w.h2, 0, sizeof(double2) * DST_MAX_VEC, s));
         const int m = w.m;
         const int64_t n = w.n;
         double beta;
@@ -431,10 +432,13 @@ struct Solver {
                 // classical Gram-Schmidt pass; ||A v_j||^2 (before) into nrm[3], ||w||^2 (after) into nrm[0]
                 if ((rc = project(nv, wv, w.h1, w.nrm + 3))) return rc;
                 if ((rc = update(nv, w.h1, wv, w.nrm))) return rc;
-                // second pass, gated on the device by the DGKS test unless always on (CGS2)
+                // second pass, gated on the device by the DGKS test unless always on
+                // (CGS2) or never (ortho 2: w.h2 stays zero)
                 const double *gate = ortho == 1 ? nullptr : w.nrm;
-                if ((rc = project(nv, wv, w.h2, nullptr, gate))) return rc;
-                if ((rc = update(nv, w.h2, wv, w.nrm, gate, true))) return rc;
+                if (ortho != 2) {
+                    if ((rc = project(nv, wv, w.h2, nullptr, gate))) return rc;
+                    if ((rc = update(nv, w.h2, wv, w.nrm, gate, true))) return rc;
+                }
                 if ((rc = scale(wv))) return rc;     // normalise on the device (1/sqrt(nrm))
                 if ((rc = read_step(nv))) return rc;
                 if (second_pass_ran() && gate) count_second_pass(nv);
@@ -557,19 +561,20 @@ struct Solver {
                           [&] { return dst_k_update_df(n, nv, Vd, c1, wv, true, nr, w.partials_r, nblk, s,
                                                        nullptr, nullptr, w.tickets + 1, vlo); })))
                 return rc;
-            // second pass, gated on the device by the DGKS test unless always on (CGS2)
+            // second pass, gated on the device by the DGKS test unless always on
+            // (CGS2) or never (ortho 2: the record's second-pass slots stay zero)
             const double *gate = ortho == 1 ? nullptr : nr;
             const double g2 = gate ? 0.0 : 1.0;
-            if ((rc = run(K_PROJECT, 1, g2 * vb * dn * (nv + 1), g2 * 8.0 * dn * nv, [&] {
+            if (ortho != 2 && (rc = run(K_PROJECT, 1, g2 * vb * dn * (nv + 1), g2 * 8.0 * dn * nv, [&] {
                      return use_tma ? dst_k_project_tma(n, nv, Vd, wv, c2, w.partials_c, nblk_tma, s, nullptr, gate,
                                                         w.tickets, nr + 7)
                                     : dst_k_project_df(n, nv, Vd, wv, !vlo, c2, w.partials_c, nblk_proj, s, nullptr,
                                                        nullptr, gate, w.tickets, vlo);
                  })))
                 return rc;
-            if ((rc = run(K_UPDATE, 1, g2 * vb * dn * (nv + 2), g2 * 8.0 * dn * nv,
-                          [&] { return dst_k_update_df(n, nv, Vd, c2, wv, !vlo, nr, w.partials_r, nblk, s, gate,
-                                                       nr + 6, w.tickets + 1, vlo); })))
+            if (ortho != 2 && (rc = run(K_UPDATE, 1, g2 * vb * dn * (nv + 2), g2 * 8.0 * dn * nv,
+                                        [&] { return dst_k_update_df(n, nv, Vd, c2, wv, !vlo, nr, w.partials_r, nblk,
+                                                                     s, gate, nr + 6, w.tickets + 1, vlo); })))
                 return rc;
             if ((rc = run(K_SCALE, 1, 2.0 * vb * dn, 6.0 * dn, [&] { return dst_k_scale_df(n, wv, nr, s, vlo); })))
                 return rc;
@@ -752,7 +757,7 @@ extern "C" int dst_default_solve_opts(dst_solve_opts *o) {
     o->inner_cycles = 1;
     o->use_initial_guess = 0;
     o->profile = 0;
-    o->ortho = 0;
+    o->ortho = 2;
     o->mixed_ortho = 2;
     o->method = 0;
     o->batch_cta_max = -1;
@@ -882,7 +887,7 @@ extern "C" int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, 
     dst_default_solve_opts(&o);
     if (opts) o = *opts;
     if (!mesh || !psi || o.restart < 1 || o.restart > DST_MAX_VEC - 1 || o.max_iters < 0 || !(o.rtol >= 0) ||
-        (o.mixed_precision && (!(o.inner_rtol > 0) || o.max_refine < 1)) || o.ortho < 0 || o.ortho > 1 ||
+        (o.mixed_precision && (!(o.inner_rtol > 0) || o.max_refine < 1)) || o.ortho < 0 || o.ortho > 2 ||
         o.mixed_ortho < 0 || o.mixed_ortho > 2 || o.inner_cycles < 0 || o.method < 0 || o.method > 1 ||
         (o.method == 1 && o.mixed_precision)) {
         rc = DST_ERR_ARG;
