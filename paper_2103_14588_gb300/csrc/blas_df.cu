@@ -709,6 +709,32 @@ __global__ void scale_df_kernel(int64_t n, float2 *__restrict__ v, const double 
     }
 }
 
+// v <- v / sqrt(*nrm2) for an FP32-stored vector (the same compensated
+// product as scale_df_kernel<false>, rounded once), two entries per 16-byte
+// access and a few CTAs per SM, each computing the FP64 factor once.
+__global__ void __launch_bounds__(256) scale_f32_kernel(int64_t n, float2 *__restrict__ v,
+                                                        const double *__restrict__ nrm2) {
+    __shared__ float s_sh[2];
+    if (threadIdx.x == 0) {
+        const double sd = 1.0 / sqrt(*nrm2);
+        s_sh[0] = (float)sd;
+        s_sh[1] = (float)(sd - (double)s_sh[0]);
+    }
+    __syncthreads();
+    const float sh = s_sh[0], sl = s_sh[1];
+    float4 *v4 = reinterpret_cast<float4 *>(v);
+    const int64_t nu = n >> 1;
+    auto sc = [&](float a) {
+        float p, e;
+        df_prod(a, 0.f, sh, sl, p, e);
+        return p + e;
+    };
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = v4[u];
+        v4[u] = make_float4(sc(a.x), sc(a.y), sc(a.z), sc(a.w));
+    }
+}
+
 // dst (df32) <- src (FP64) / sqrt(*nrm2): the restart vector of a cycle
 // (VL = false: rounded to FP32).
 template <bool VL>
@@ -821,8 +847,14 @@ int dst_k_update_df(int64_t n, int nvec, const float2 *V, const double2 *h, floa
 }
 
 int dst_k_scale_df(int64_t n, float2 *v, const double *nrm2, cudaStream_t s, bool vlo) {
-    if (vlo) scale_df_kernel<true><<<df_stream_blocks(n), 256, 0, s>>>(n, v, nrm2);
-    else scale_df_kernel<false><<<df_stream_blocks(n), 256, 0, s>>>(n, v, nrm2);
+    if (vlo) {
+        scale_df_kernel<true><<<df_stream_blocks(n), 256, 0, s>>>(n, v, nrm2);
+    } else {
+        if (n & 1) return DST_ERR_ARG;          // two entries per 16-byte access
+        int64_t b = (n / 2 + 255) / 256;
+        if (b > 4 * 152) b = 4 * 152;
+        scale_f32_kernel<<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(n, v, nrm2);
+    }
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
