@@ -185,7 +185,7 @@ typedef struct {
     int profile;            /* 1: time every kernel class with CUDA events (small overhead) */
     int inner_cycles;       /* GMRES(m) cycles per refinement step (mixed only; 0 = until
                                inner_rtol), default 1 */
-    int ortho;              /* Gram-Schmidt (default 2): 0 = classical, second pass only when the DGKS test
+    int ortho;              /* Gram-Schmidt (default 0): 0 = classical, second pass only when the DGKS test
                                asks (norm fell below 1/sqrt 2 of its value before the pass);
                                1 = always two classical passes (CGS2); 2 = one classical pass,
                                never reorthogonalised (PETSc's default for GMRES) */
@@ -237,8 +237,8 @@ typedef struct {
 
 /* Fill opts with the defaults (restart 30, max_iters 100000, rtol 1e-8,
  * FP64, inner_rtol 1e-4, max_refine 100000, zero initial guess, no
- * profiling, one inner cycle per refinement, one classical Gram-Schmidt pass
- * without reorthogonalisation, inner Gram-Schmidt on an FP32-stored basis in
+ * profiling, one inner cycle per refinement, classical Gram-Schmidt with a
+ * DGKS-selective second pass, inner Gram-Schmidt on an FP32-stored basis in
  * compensated arithmetic, GMRES). */
 DST_API int dst_default_solve_opts(dst_solve_opts *opts);
 

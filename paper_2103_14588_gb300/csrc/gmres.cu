@@ -757,7 +757,7 @@ extern "C" int dst_default_solve_opts(dst_solve_opts *o) {
     o->inner_cycles = 1;
     o->use_initial_guess = 0;
     o->profile = 0;
-    o->ortho = 2;
+    o->ortho = 0;
     o->mixed_ortho = 2;
     o->method = 0;
     o->batch_cta_max = -1;

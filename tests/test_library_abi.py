@@ -70,7 +70,7 @@ def test_argument_errors_without_device(B):
 def test_default_opts(B):
     o = B.dst_default_solve_opts()
     assert o.restart == 30 and o.rtol == 1e-8 and o.mixed_precision == 0 and o.use_initial_guess == 0
-    assert o.mixed_ortho == 2 and o.method == 0 and o.inner_cycles == 1 and o.ortho == 2
+    assert o.mixed_ortho == 2 and o.method == 0 and o.inner_cycles == 1 and o.ortho == 0
 
 
 def test_product_package_does_not_use_oracle():
