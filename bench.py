@@ -93,6 +93,22 @@ def oracle_seconds_per_step(w, k=4):
     return max((t2 - t1) - (t1 - t0), 1e-9) / k
 
 
+def replica_seed(rank):
+    """Seed of the bench workload on a rank: independent replicas draw independent packets."""
+    return 20210326 + rank
+
+
+def aggregate_timing(t_ms, world, steps, dist=None, device="cuda"):
+    """Length of the timed region as the maximum over ranks, and the whole-job
+    throughput (solves of all ranks per second of that region)."""
+    if world > 1:
+        import torch
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    return t_ms, world * steps / (t_ms * 1e-3)
+
+
 def host_cores():
     return os.cpu_count() or 1
 
@@ -340,7 +356,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    w = W.zb_2p1(seed=20210326 + rank)
+    w = W.zb_2p1(seed=replica_seed(rank))
     mesh_obj = B.Mesh.from_workload(w)
     mesh = mesh_obj.handle
     n = mesh_obj.n_unknowns
@@ -372,12 +388,7 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         barrier()
-    t_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = tt.item()
-    value = world * args.steps / (t_ms * 1e-3)
+    t_ms, value = aggregate_timing(e0.elapsed_time(e1), world, args.steps, dist)
     for s in stats:
         if s["status"] != 0:
             raise RuntimeError("timed solve did not converge: %s" % s)
