@@ -182,7 +182,8 @@ typedef struct {
     double inner_rtol;      /* inner relative tolerance per refinement step (mixed only) */
     int max_refine;         /* cap on refinement steps (mixed only) */
     int use_initial_guess;  /* 1: psi holds x0 on entry; 0: start from zero */
-    int profile;            /* 1: time every kernel class with CUDA events (small overhead) */
+    int profile;            /* 1: time every kernel with CUDA events (one event between
+                               consecutive kernels; ~10% overhead on small meshes) */
     int inner_cycles;       /* GMRES(m) cycles per refinement step (mixed only; 0 = until
                                inner_rtol), default 1 */
     int ortho;              /* Gram-Schmidt (default 0): 0 = classical, second pass only when the DGKS test
@@ -194,9 +195,11 @@ typedef struct {
                                FP32 products and sums, FP64 reductions; needs inner_cycles = 1),
                                1 = native FP64 (FP64 basis),
                                2 = FP32-stored basis (8 B per entry, half the traffic of 0) with
-                               the same error-free products and compensated sums: inner products
-                               and updates are FP64-class on the stored values, each new basis
-                               vector is rounded to FP32 once (needs inner_cycles = 1) */
+                               exact FP32 products and compensated sums: inner products and
+                               updates of the stored values carry about 45 bits relative to the
+                               sum of the terms' magnitudes, each new basis vector is rounded to
+                               FP32 once; from 4M unknowns the projection is fed by bulk
+                               asynchronous copies (needs inner_cycles = 1) */
     int method;             /* Krylov method: 0 = restarted GMRES(restart) (default),
                                1 = BiCGSTAB (van der Vorst 1992; FP64 only, mixed_precision
                                must be 0; iters counts BiCGSTAB steps of two applies each) */
