@@ -110,6 +110,20 @@ def aggregate_timing(t_ms, world, steps, dist=None, device="cuda"):
 
 
 def host_cores():
+    """Threads the oracle's numpy / BLAS work may use on this host (its dense element
+    products are BLAS matrix products): the BLAS pool size where threadpoolctl is
+    installed, else the usual thread-count variables, else the core count."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var)
+        if v and v.isdigit() and int(v) > 0:
+            return int(v)
     return os.cpu_count() or 1
 
 
