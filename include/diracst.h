@@ -51,12 +51,14 @@
 extern "C" {
 #endif
 
-/* Status codes. */
+/* Status codes.  No C++ exception crosses this interface: a failed host
+ * allocation or host thread start inside a call returns DST_ERR_OOM, with the
+ * reason in dst_last_error_detail(). */
 enum {
     DST_OK = 0,
     DST_NOT_CONVERGED = 1,   /* solve hit max_iters; psi holds the best iterate */
     DST_ERR_ARG = -1,        /* invalid argument (null pointer, bad size, bad enum) */
-    DST_ERR_OOM = -2,        /* device or host allocation failed */
+    DST_ERR_OOM = -2,        /* device or host allocation (or host thread start) failed */
     DST_ERR_CUDA = -3,       /* a CUDA runtime call failed */
     DST_ERR_NAN = -5,        /* non-finite value met in the right-hand side or residual */
     DST_ERR_STATE = -6       /* required input not set yet (e.g. initial data) */
@@ -100,7 +102,8 @@ DST_API int dst_set_mass(dst_mesh *mesh, double m);
  * from HOST memory: nel_x * nel_y * nel_z doubles, x fastest, each the value
  * at the element centroid; NULL resets V to zero.  A potential that depends
  * on x only takes the fast separable path; any other takes a general path.
- * Errors: DST_ERR_ARG (non-finite value), DST_ERR_OOM, DST_ERR_CUDA.
+ * Errors: DST_ERR_ARG (non-finite value), DST_ERR_OOM, DST_ERR_CUDA; after
+ * DST_ERR_ARG or DST_ERR_OOM the previous potential stays in force.
  */
 DST_API int dst_set_potential(dst_mesh *mesh, const double *V_elem);
 
@@ -293,7 +296,8 @@ DST_API int dst_get_apply_variant(const dst_mesh *mesh, int precision, int *vari
  * one CTA each inside a single persistent kernel launch per spatial dimension,
  * without host involvement until all of them finish; larger meshes are solved
  * by single-mesh solves running concurrently from worker threads, each on a
- * stream of its own (the meshes must not be used by other threads meanwhile).
+ * stream of its own (the meshes must not be used by other threads meanwhile;
+ * if no worker thread can be started, the calling thread solves them).
  * Used from opts: restart (1..32), max_iters and max_refine (per mesh), rtol,
  * inner_rtol, ortho, use_initial_guess, batch_cta_max; method must be 0;
  * mixed_precision, inner_cycles, mixed_ortho and profile are ignored.  The

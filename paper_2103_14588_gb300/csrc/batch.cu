@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <mutex>
 #include <thread>
 #include <cmath>
 #include <cstdint>
@@ -446,8 +447,8 @@ using namespace dst;
 constexpr int64_t BATCH_CTA_MAX_AUTO = 4096;
 constexpr int BATCH_WORKERS = 16;          // concurrent single-mesh solves (one stream each)
 
-extern "C" int dst_solve_batch(int count, dst_mesh *const *meshes, const dst_solve_opts *opts, void *const *psi,
-                               dst_solve_stats *stats, void *stream) {
+static int solve_batch(int count, dst_mesh *const *meshes, const dst_solve_opts *opts, void *const *psi,
+                       dst_solve_stats *stats, void *stream) {
     if (count <= 0 || !meshes || !opts || !psi || !stats) return DST_ERR_ARG;
     const dst_solve_opts &u = *opts;
     if (u.restart < 1 || u.restart > BMAXM || u.max_iters < 1 || u.max_refine < 1 || !(u.rtol > 0) ||
@@ -479,42 +480,51 @@ extern "C" int dst_solve_batch(int count, dst_mesh *const *meshes, const dst_sol
     std::sort(small.begin(), small.end(), by_size);
     std::sort(big.begin(), big.end(), by_size);
     std::vector<int> rcs(count, DST_OK);
+    const int cs_ = (int)small.size();
+    // host memory of the small-mesh path, taken before any worker starts
+    std::vector<BatchInst> packed;
+    packed.reserve(cs_);
+    std::vector<double> outs((size_t)cs_ * 8, 0.0);
+    std::vector<std::thread> workers;
+    const int nw = std::min<int>((int)big.size(), BATCH_WORKERS);
+    workers.reserve(nw);
     cudaEvent_t start = nullptr;
     DST_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
     cudaEventRecord(start, s);
     // large meshes: single-mesh mixed solves, BATCH_WORKERS at a time on their own streams
-    std::vector<std::thread> workers;
     std::atomic<int> next{0};
-    const int nw = std::min<int>((int)big.size(), BATCH_WORKERS);
+    auto worker = [&] {
+        cudaSetDevice(dev);
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+            for (int k = next++; k < (int)big.size(); k = next++) rcs[big[k]] = DST_ERR_CUDA;
+            return;
+        }
+        cudaStreamWaitEvent(ws, start, 0);
+        dst_solve_opts o1 = u;
+        o1.mixed_precision = 1;
+        o1.mixed_ortho = 2;
+        o1.inner_cycles = 1;
+        o1.profile = 0;
+        for (int k = next++; k < (int)big.size(); k = next++) {
+            const int i = big[k];
+            rcs[i] = dst_solve(meshes[i], &o1, psi[i], &stats[i], ws);
+        }
+        cudaStreamDestroy(ws);
+    };
     for (int w = 0; w < nw; ++w) {
-        workers.emplace_back([&] {
-            cudaSetDevice(dev);
-            cudaStream_t ws = nullptr;
-            if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
-                for (int k = next++; k < (int)big.size(); k = next++) rcs[big[k]] = DST_ERR_CUDA;
-                return;
-            }
-            cudaStreamWaitEvent(ws, start, 0);
-            dst_solve_opts o1 = u;
-            o1.mixed_precision = 1;
-            o1.mixed_ortho = 2;
-            o1.inner_cycles = 1;
-            o1.profile = 0;
-            for (int k = next++; k < (int)big.size(); k = next++) {
-                const int i = big[k];
-                rcs[i] = dst_solve(meshes[i], &o1, psi[i], &stats[i], ws);
-            }
-            cudaStreamDestroy(ws);
-        });
+        try {
+            workers.emplace_back(worker);
+        } catch (...) {
+            break;      // fewer workers: those running take every large mesh between them
+        }
     }
     int rc = DST_OK;
-    // small meshes: one CTA each in the persistent kernel
-    const int cs_ = (int)small.size();
-    std::vector<BatchInst> packed;
+    // small meshes: one CTA each in the persistent kernel.  No exception leaves
+    // this block while workers run (they use this frame's locals).
     char *wsb = nullptr;
-    std::vector<double> outs((size_t)cs_ * 8, 0.0);
     int c1 = 0;
-    if (cs_ > 0) {
+    if (cs_ > 0) try {
         const int m = u.restart;
         std::vector<size_t> off(cs_);
         size_t total = align256(sizeof(BatchInst) * cs_);
@@ -571,12 +581,19 @@ extern "C" int dst_solve_batch(int count, dst_mesh *const *meshes, const dst_sol
             cudaMemcpyAsync(d_inst, packed.data(), sizeof(BatchInst) * cs_, cudaMemcpyHostToDevice, s) != cudaSuccess)
             rc = DST_ERR_CUDA;
         BatchOpts bo{m, u.max_iters, u.max_refine, u.use_initial_guess, u.ortho, u.rtol, u.inner_rtol};
+        // one side stream per device for the 2+1 kernel, shared by concurrent calls
         static cudaStream_t side[DST_MAX_DEVICES_APPLY] = {};
+        static std::mutex side_mu;
         const int c2 = cs_ - c1;
         if (rc == DST_OK && c1 > 0 && c2 > 0) {
             cudaEvent_t fork = nullptr, join = nullptr;
-            if (!side[dev] && cudaStreamCreateWithFlags(&side[dev], cudaStreamNonBlocking) != cudaSuccess)
-                rc = DST_ERR_CUDA;
+            {
+                std::lock_guard<std::mutex> lk(side_mu);
+                if (!side[dev] && cudaStreamCreateWithFlags(&side[dev], cudaStreamNonBlocking) != cudaSuccess) {
+                    side[dev] = nullptr;
+                    rc = DST_ERR_CUDA;
+                }
+            }
             if (rc == DST_OK && (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
                                  cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess))
                 rc = DST_ERR_CUDA;
@@ -598,7 +615,14 @@ extern "C" int dst_solve_batch(int count, dst_mesh *const *meshes, const dst_sol
             if (cudaMemcpyAsync(outs.data() + 8 * q, packed[q].out, sizeof(double) * 8, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess)
                 rc = DST_ERR_CUDA;
+    } catch (const std::exception &e) {
+        dst_internal_set_exception_detail("dst_solve_batch", e.what());
+        if (rc == DST_OK) rc = DST_ERR_OOM;
+    } catch (...) {
+        dst_internal_set_exception_detail("dst_solve_batch", "unknown C++ exception");
+        if (rc == DST_OK) rc = DST_ERR_OOM;
     }
+    if (workers.empty() && !big.empty()) worker();      // no thread could be started
     for (auto &t : workers) t.join();
     cudaError_t se = cudaStreamSynchronize(s);
     if (rc == DST_OK && se != cudaSuccess) rc = DST_ERR_CUDA;
@@ -625,4 +649,10 @@ extern "C" int dst_solve_batch(int count, dst_mesh *const *meshes, const dst_sol
         if (rcs[i] < 0 && (worst == DST_OK || rcs[i] < worst)) worst = rcs[i];
     }
     return worst;
+}
+
+extern "C" int dst_solve_batch(int count, dst_mesh *const *meshes, const dst_solve_opts *opts, void *const *psi,
+                               dst_solve_stats *stats, void *stream) {
+    return dst_internal_guard("dst_solve_batch",
+                              [&] { return solve_batch(count, meshes, opts, psi, stats, stream); });
 }

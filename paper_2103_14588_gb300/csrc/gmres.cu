@@ -664,21 +664,39 @@ struct Solver {
 };
 
 // A private stream per thread for capturing (the caller's stream may be the
-// legacy default stream, which cannot be captured).
+// legacy default stream, which cannot be captured).  It is destroyed when its
+// thread exits, so that short-lived threads (the batch call's workers) leave no
+// streams behind.
+struct ThreadCaptureStream {
+    cudaStream_t s = nullptr;
+    int dev = -1;
+    void release() {
+        if (!s) return;
+        int prev = -1;
+        const bool have_prev = cudaGetDevice(&prev) == cudaSuccess;
+        cudaSetDevice(dev);
+        cudaStreamDestroy(s);
+        if (have_prev) cudaSetDevice(prev);
+        cudaGetLastError();
+        s = nullptr;
+    }
+    ~ThreadCaptureStream() { release(); }
+};
+
 static cudaStream_t capture_stream() {
-    static thread_local cudaStream_t cs = nullptr;
-    static thread_local int cs_dev = -1;
+    static thread_local ThreadCaptureStream tl;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    if (!cs || cs_dev != dev) {
-        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    if (!tl.s || tl.dev != dev) {
+        tl.release();
+        if (cudaStreamCreateWithFlags(&tl.s, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
-            cs = nullptr;
+            tl.s = nullptr;
             return nullptr;
         }
-        cs_dev = dev;
+        tl.dev = dev;
     }
-    return cs;
+    return tl.s;
 }
 
 int CycleGraph::capture(Solver &sv, int steps, bool vlo) {
@@ -701,7 +719,11 @@ int CycleGraph::capture(Solver &sv, int steps, bool vlo) {
         return DST_OK;
     }
     p.capturing = true;
-    rc = sv.enqueue_steps(steps, vlo);
+    try {
+        rc = sv.enqueue_steps(steps, vlo);
+    } catch (...) {
+        rc = DST_ERR_OOM;      // a failed host allocation: the capture still ends below
+    }
     p.capturing = false;
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &g);
@@ -894,7 +916,8 @@ extern "C" int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, 
     } else if (!mesh->d_psi0) {
         rc = DST_ERR_STATE;
     } else {
-        rc = solve_impl(mesh, o, (double2 *)psi, st, (cudaStream_t)stream);
+        rc = dst_internal_guard("dst_solve",
+                                [&] { return solve_impl(mesh, o, (double2 *)psi, st, (cudaStream_t)stream); });
     }
     st.status = rc;
     st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

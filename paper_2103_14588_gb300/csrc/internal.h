@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
 #include <vector>
 
 #include "../../include/diracst.h"
@@ -19,6 +20,23 @@
 
 void dst_internal_set_cuda_error(cudaError_t e, const char *expr, const char *file, int line);
 void dst_internal_set_error_detail(const char *msg);
+void dst_internal_set_exception_detail(const char *call, const char *what);
+
+// Runs the body of a C ABI entry point that allocates host memory or starts
+// host threads, so that no C++ exception crosses the C ABI: the only ones these
+// bodies can raise are a failed host allocation or thread start, returned as
+// DST_ERR_OOM with the exception's text as the error detail.
+template <class F>
+int dst_internal_guard(const char *call, F &&body) noexcept {
+    try {
+        return body();
+    } catch (const std::exception &e) {
+        dst_internal_set_exception_detail(call, e.what());
+    } catch (...) {
+        dst_internal_set_exception_detail(call, "unknown C++ exception");
+    }
+    return DST_ERR_OOM;
+}
 
 // Geometry of one spatial axis, as the kernels see it.
 struct AxisDesc {

@@ -18,6 +18,11 @@ void dst_internal_set_error_detail(const char *msg) {
     snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s", msg);
 }
 
+void dst_internal_set_exception_detail(const char *call, const char *what) {
+    snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: host allocation or thread start failed: %s", call,
+             what);
+}
+
 extern "C" const char *dst_last_error_detail(void) { return g_last_cuda_error; }
 
 extern "C" const char *dst_status_string(int status) {
@@ -124,22 +129,38 @@ extern "C" int dst_get_apply_variant(const dst_mesh *mesh, int precision, int *v
 }
 
 // Separable weights (m*beta + V_ex) per x element for beta = +1 and -1.  Only
-// valid when V does not vary along y and z (or is zero).
-int dst_internal_update_weights(dst_mesh *mesh) {
+// valid when V does not vary along y and z (or is zero).  Building them is the
+// only step that can run out of host memory; uploading changes the mesh.
+static int build_weights(const dst_mesh *mesh, double m, const std::vector<double> &V, std::vector<double> &w) {
     const int64_t nx = mesh->nel[0];
-    std::vector<double> w(2 * nx);
-    for (int64_t e = 0; e < nx; ++e) {
-        double v = mesh->V.empty() ? 0.0 : mesh->V[e];
-        w[e] = mesh->m + v;
-        w[nx + e] = -mesh->m + v;
+    try {
+        w.resize(2 * nx);
+    } catch (const std::exception &ex) {
+        dst_internal_set_exception_detail("dst weights", ex.what());
+        return DST_ERR_OOM;
     }
+    for (int64_t e = 0; e < nx; ++e) {
+        double v = V.empty() ? 0.0 : V[e];
+        w[e] = m + v;
+        w[nx + e] = -m + v;
+    }
+    return DST_OK;
+}
+
+static int upload_weights(dst_mesh *mesh, const std::vector<double> &w) {
     int dev_prev;
     DST_CUDA_TRY(cudaGetDevice(&dev_prev));
     DST_CUDA_TRY(cudaSetDevice(mesh->device));
-    cudaError_t e = cudaMemcpy(mesh->d_wx, w.data(), sizeof(double) * 2 * nx, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(mesh->d_wx, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice);
     cudaSetDevice(dev_prev);
     DST_CUDA_TRY(e);
     return DST_OK;
+}
+
+int dst_internal_update_weights(dst_mesh *mesh) {
+    std::vector<double> w;
+    const int rc = build_weights(mesh, mesh->m, mesh->V, w);
+    return rc != DST_OK ? rc : upload_weights(mesh, w);
 }
 
 extern "C" int dst_create_mesh(int d, const int64_t n_el[4], const double lo[4], const double hi[4],
@@ -228,32 +249,34 @@ extern "C" int dst_mesh_sizes(const dst_mesh *mesh, int64_t *n_spatial_nodes, in
 
 extern "C" int dst_set_mass(dst_mesh *mesh, double m) {
     if (!mesh || !std::isfinite(m)) return DST_ERR_ARG;
-    mesh->m = m;
-    return dst_internal_update_weights(mesh);
+    std::vector<double> w;
+    int rc = build_weights(mesh, m, mesh->V, w);
+    if (rc == DST_OK) rc = upload_weights(mesh, w);
+    if (rc == DST_OK) mesh->m = m;
+    return rc;
 }
 
-extern "C" int dst_set_potential(dst_mesh *mesh, const double *V_elem) {
-    if (!mesh) return DST_ERR_ARG;
+// The mesh changes only once every step that can fail for want of memory has
+// succeeded, so that DST_ERR_OOM leaves the previous potential in force and a
+// general potential never goes without its device copy.
+static int set_potential(dst_mesh *mesh, const double *V_elem) {
     const int64_t nx = mesh->nel[0], nyz = mesh->nel[1] * mesh->nel[2];
-    if (!V_elem) {
-        mesh->V.clear();
-        mesh->v_general = false;
-        return dst_internal_update_weights(mesh);
-    }
-    const int64_t ne = nx * nyz;
+    const int64_t ne = V_elem ? nx * nyz : 0;
     for (int64_t i = 0; i < ne; ++i)
         if (!std::isfinite(V_elem[i])) return DST_ERR_ARG;
-    mesh->V.assign(V_elem, V_elem + ne);
+    std::vector<double> V(V_elem, V_elem + ne), w;
     bool general = false;
-    for (int64_t j = 1; j < nyz && !general; ++j)
+    for (int64_t j = 1; j < nyz && ne && !general; ++j)
         for (int64_t e = 0; e < nx; ++e)
             if (V_elem[j * nx + e] != V_elem[e]) { general = true; break; }
-    mesh->v_general = general;
+    int rc = build_weights(mesh, mesh->m, V, w);
+    if (rc != DST_OK) return rc;
     if (general) {
         int dev_prev;
         DST_CUDA_TRY(cudaGetDevice(&dev_prev));
         DST_CUDA_TRY(cudaSetDevice(mesh->device));
         if (!mesh->d_V && cudaMalloc(&mesh->d_V, sizeof(double) * ne) != cudaSuccess) {
+            cudaGetLastError();
             mesh->d_V = nullptr;
             cudaSetDevice(dev_prev);
             return DST_ERR_OOM;
@@ -262,17 +285,25 @@ extern "C" int dst_set_potential(dst_mesh *mesh, const double *V_elem) {
         cudaSetDevice(dev_prev);
         DST_CUDA_TRY(e);
     }
-    return dst_internal_update_weights(mesh);
+    if ((rc = upload_weights(mesh, w)) != DST_OK) return rc;
+    mesh->V.swap(V);
+    mesh->v_general = general;
+    return DST_OK;
 }
 
-extern "C" int dst_set_initial_data(dst_mesh *mesh, const double *psi0) {
-    if (!mesh || !psi0) return DST_ERR_ARG;
+extern "C" int dst_set_potential(dst_mesh *mesh, const double *V_elem) {
+    if (!mesh) return DST_ERR_ARG;
+    return dst_internal_guard("dst_set_potential", [&] { return set_potential(mesh, V_elem); });
+}
+
+static int set_initial_data(dst_mesh *mesh, const double *psi0) {
     const int64_t n = mesh->n_spatial * mesh->nc * 2;
     mesh->psi0.assign(psi0, psi0 + n);
     int dev_prev;
     DST_CUDA_TRY(cudaGetDevice(&dev_prev));
     DST_CUDA_TRY(cudaSetDevice(mesh->device));
     if (!mesh->d_psi0 && cudaMalloc(&mesh->d_psi0, sizeof(double) * n) != cudaSuccess) {
+        cudaGetLastError();
         mesh->d_psi0 = nullptr;
         cudaSetDevice(dev_prev);
         return DST_ERR_OOM;
@@ -281,6 +312,11 @@ extern "C" int dst_set_initial_data(dst_mesh *mesh, const double *psi0) {
     cudaSetDevice(dev_prev);
     DST_CUDA_TRY(e);
     return DST_OK;
+}
+
+extern "C" int dst_set_initial_data(dst_mesh *mesh, const double *psi0) {
+    if (!mesh || !psi0) return DST_ERR_ARG;
+    return dst_internal_guard("dst_set_initial_data", [&] { return set_initial_data(mesh, psi0); });
 }
 
 int dst_internal_apply(const dst_mesh *mesh, int precision, const void *x, void *y, cudaStream_t s) {

@@ -214,3 +214,33 @@ def test_tune_apply_and_errors(torch, B):
             with pytest.raises(B.DstError) as e:
                 B.dst_set_apply_variant(*args)
             assert e.value.code == B.DST_ERR_ARG
+
+
+@pytest.mark.parametrize("d,n_el,bc,kind", [(1, [40, 1, 1, 6], [P], "xonly"), (2, [12, 10, 1, 5], [P, D], "general")])
+def test_rejected_setters_keep_the_operator(torch, B, d, n_el, bc, kind):
+    """A potential or a mass that the library rejects (a non-finite value) leaves
+    the operator as it was, for the x-only and for the general potential kernel;
+    a valid change afterwards still takes effect."""
+    w = W.random_mesh(d, n_el, bc, seed=21, with_potential=False)
+    w.V = _potential(d, n_el, kind, 22)
+    with B.Mesh.from_workload(w) as mesh:
+        x = torch.from_numpy(W.random_complex(mesh.n_unknowns, 23)).cuda()
+
+        def apply():
+            y = torch.full_like(x, float("nan"))
+            B.dst_apply_operator(mesh.handle, B.DST_FP64, x, y)
+            torch.cuda.synchronize()
+            return y
+
+        y0 = apply()
+        bad = np.array(w.V, dtype=np.float64)
+        bad[-1] = np.nan
+        with pytest.raises(B.DstError) as e:
+            B.dst_set_potential(mesh.handle, bad)
+        assert e.value.code == B.DST_ERR_ARG
+        with pytest.raises(B.DstError) as e:
+            B.dst_set_mass(mesh.handle, float("inf"))
+        assert e.value.code == B.DST_ERR_ARG
+        assert torch.equal(apply(), y0)
+        B.dst_set_mass(mesh.handle, w.m + 0.5)
+        assert not torch.equal(apply(), y0)

@@ -145,3 +145,24 @@ def test_batch_rejects_unsupported(torch, B):
     finally:
         for m in (m1, m3, mg):
             m.close()
+
+
+def test_batch_repeated_calls_identical(torch, B):
+    """Three calls in a row (fresh worker threads each time, whose capture streams are
+    released when they exit) give the same solutions bit for bit."""
+    ws = _meshes()[3:]
+    meshes = [B.Mesh.from_workload(w) for w in ws]
+    try:
+        runs = []
+        for _ in range(3):
+            psis = [torch.zeros(m.n_unknowns, dtype=torch.complex128, device="cuda") for m in meshes]
+            rc, sts = B.dst_solve_batch([m.handle for m in meshes],
+                                        {"rtol": 1e-11, "max_iters": 100000, "batch_cta_max": 0}, psis)
+            torch.cuda.synchronize()
+            assert rc == 0 and all(s["status"] == 0 for s in sts)
+            runs.append(psis)
+        for r in runs[1:]:
+            assert all(torch.equal(a, b) for a, b in zip(r, runs[0]))
+    finally:
+        for m in meshes:
+            m.close()
