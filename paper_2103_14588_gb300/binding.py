@@ -178,6 +178,8 @@ def dst_set_mass(mesh, m):
 
 
 def dst_set_potential(mesh, V):
+    """V: one value per spatial element, x fastest (nel_x * nel_y * nel_z values;
+    the C library reads exactly that many), or None for no potential."""
     if V is None:
         return _check(_lib.dst_set_potential(mesh, None), "dst_set_potential")
     arr = np.ascontiguousarray(V, dtype=np.float64)
@@ -328,6 +330,13 @@ class Mesh:
     """Owning wrapper of a mesh handle built from a workload-like description."""
 
     def __init__(self, d, n_el, lo, hi, bc, m=None, V=None, psi0=None):
+        if V is not None:
+            ne = 1
+            for k in range(int(d)):
+                ne *= int(n_el[k])
+            if np.size(V) != ne:
+                raise ValueError("V needs one value per spatial element (%d), got %d" % (ne, np.size(V)))
+        self.handle = None
         self.handle = dst_create_mesh(d, n_el, lo, hi, bc)
         self.n_spatial, self.n_unknowns, self.ncomp = dst_mesh_sizes(self.handle)
         if m is not None:

@@ -67,6 +67,37 @@ def test_argument_errors_without_device(B):
     assert lib.dst_destroy_mesh(None) == B.DST_OK
 
 
+def test_every_call_rejects_missing_arguments_without_device(B):
+    """Each entry point checks its pointers and sizes before any CUDA call."""
+    import ctypes
+    lib = B.library()
+    ARG = B.DST_ERR_ARG
+    assert lib.dst_mesh_sizes(None, None, None, None) == ARG
+    assert lib.dst_set_mass(None, 1.0) == ARG
+    assert lib.dst_set_potential(None, None) == ARG
+    assert lib.dst_set_initial_data(None, None) == ARG
+    assert lib.dst_build_rhs(None, None, None) == ARG
+    assert lib.dst_arnoldi_update(0, 1, None, None, None, None, None) == ARG
+    assert lib.dst_arnoldi_project_noalloc(0, 1, None, None, None, None) == ARG
+    assert lib.dst_observables(None, None, 0.0, None, None) == ARG
+    assert lib.dst_default_solve_opts(None) == ARG
+    assert lib.dst_solve_batch(0, None, None, None, None, None) == ARG
+    assert lib.dst_tune_apply(None, None) == ARG
+    assert lib.dst_set_apply_variant(None, 0, 0) == ARG
+    v, c = ctypes.c_int(), ctypes.c_int()
+    assert lib.dst_get_apply_variant(None, 0, ctypes.byref(v), ctypes.byref(c)) == ARG
+
+
+def test_mesh_wrapper_checks_potential_length(B):
+    """The C library reads nel_x * nel_y * nel_z potential values; the wrapper refuses
+    another length before it creates a mesh."""
+    import numpy as np
+    with pytest.raises(ValueError):
+        B.Mesh(2, [4, 3, 1, 2], [0, 0, 0, 0], [1, 1, 1, 1], [0, 0, 0], V=np.zeros(11))
+    with pytest.raises(ValueError):
+        B.Mesh(1, [8, 1, 1, 2], [0, 0, 0, 0], [1, 1, 1, 1], [0, 0, 0], V=np.zeros(9))
+
+
 def test_default_opts(B):
     o = B.dst_default_solve_opts()
     assert o.restart == 30 and o.rtol == 1e-8 and o.mixed_precision == 0 and o.use_initial_guess == 0

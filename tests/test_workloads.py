@@ -75,3 +75,21 @@ def test_batch_instances_draws():
         dens = np.sum(np.abs(w.psi0) ** 2)
         h = np.prod([(w.hi[k] - w.lo[k]) / w.n_el[k] for k in range(w.d)])
         assert abs(dens * h - 1.0) < 1e-12
+
+
+def test_every_generator_sizes_its_data():
+    """Each generator's potential has one value per spatial element (x fastest) and
+    its psi0 one spinor per unknown spatial node: the lengths the C library reads."""
+    P, O, D = W.PERIODIC, W.OPEN, W.DIRICHLET
+    ws = [W.plane_wave_1p1(n=16), W.zb_2p1(n=8, nt=4), W.klein_3p1(n=6, nt=3),
+          W.sommerfeld_1p1(n=32, nt=8, L=0.25), W.random_mesh(2, [5, 4, 1, 3], [O, D], seed=1),
+          W.random_mesh(3, [3, 4, 5, 2], [P, O, D], seed=2)]
+    ws += W.batch_instances(count=6, seed=3, n1=(8, 16), n2=(6, 8))
+    for w in ws:
+        nel = [w.n_el[k] if k < w.d else 1 for k in range(3)]
+        if w.V is not None:
+            assert np.size(w.V) == nel[0] * nel[1] * nel[2], w.name
+        nu = [1, 1, 1]
+        for k in range(w.d):
+            nu[k] = {P: nel[k], O: nel[k] + 1, D: nel[k] - 1}[w.bc[k]]
+        assert np.size(w.psi0) == nu[0] * nu[1] * nu[2] * (2 if w.d < 3 else 4), w.name
