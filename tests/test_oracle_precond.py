@@ -1,0 +1,75 @@
+"""Pins of the oracle's non-learned preconditioners.
+
+Each is the exact inverse of a matrix that is block diagonal in its own blocks:
+the node blocks for block Jacobi, the (overlap-extended) time slabs for the
+Schwarz method.  Such matrices are built here by masking the assembled D_w22
+by block index, so a wrong block size, a slab offset off by a layer or a
+restriction that keeps the overlap fails.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import mesh as M, operator as OP, precond as PC, solvers as SO
+
+
+def _system(d, nel, nt, bc, seed):
+    rng = np.random.default_rng(seed)
+    me = M.Mesh(d, list(nel) + [nt], [0, 0, 0, 0], [1.0, 1.0, 1.0, 0.5], bc)
+    psi0 = rng.standard_normal(me.spatial_shape) + 1j * rng.standard_normal(me.spatial_shape)
+    V = rng.uniform(0, 1, me.nel[0] * me.nel[1] * me.nel[2])
+    A, b = OP.split(me, OP.assemble(me, 1.0, V), psi0)
+    return me, A.tocsr(), b
+
+
+def _mask(A, block_of):
+    """Keep the entries (i, j) of A with block_of[i] == block_of[j]."""
+    C = A.tocoo()
+    keep = block_of[C.row] == block_of[C.col]
+    return sp.csr_matrix((C.data[keep], (C.row[keep], C.col[keep])), shape=A.shape)
+
+
+@pytest.mark.parametrize("d,nel,bc", [(1, (9, 1, 1), [M.OPEN]), (2, (5, 4, 1), [M.PERIODIC, M.DIRICHLET]),
+                                      (3, (3, 3, 2), [M.PERIODIC, M.OPEN, M.PERIODIC])])
+def test_node_block_jacobi_inverts_node_block_diagonal(d, nel, bc):
+    me, A, b = _system(d, nel, 3, bc, seed=d)
+    n = A.shape[0]
+    node = np.arange(n) // me.nc
+    Abd = _mask(A, node)
+    Mj = PC.node_block_jacobi(me.nc, A)
+    v = np.random.default_rng(9).standard_normal(n) + 0j
+    np.testing.assert_allclose(Mj(Abd @ v), v, rtol=0, atol=1e-11 * np.abs(v).max())
+    # the blocks are the diagonal ones: off-block entries of A do not enter
+    Mbd = PC.node_block_jacobi(me.nc, Abd)
+    np.testing.assert_array_equal(Mj(b), Mbd(b))
+
+
+@pytest.mark.parametrize("S,overlap", [(1, 0), (2, 0), (3, 1), (4, 2), (7, 0)])
+def test_time_slab_schwarz_inverts_slab_block_diagonal(S, overlap):
+    nt = 7
+    me, A, b = _system(2, (4, 3, 1), nt, [M.PERIODIC, M.OPEN], seed=11)
+    per = me.n_spatial_nodes * me.nc
+    slab = (np.arange(A.shape[0]) // per) // S
+    Abd = _mask(A, slab)
+    Ms = PC.time_slab_schwarz(Abd, nt, per, S, overlap)
+    v = np.random.default_rng(12).standard_normal(A.shape[0]) + 1j
+    np.testing.assert_allclose(Ms(Abd @ v), v, rtol=0, atol=1e-10 * np.abs(v).max())
+
+
+def test_one_slab_is_the_exact_inverse():
+    nt = 6
+    me, A, b = _system(1, (10, 1, 1), nt, [M.DIRICHLET], seed=13)
+    per = me.n_spatial_nodes * me.nc
+    x_lu = SO.dense_solve(A, b)
+    Ms = PC.time_slab_schwarz(A, nt, per, nt, 0)
+    np.testing.assert_allclose(Ms(b), x_lu, rtol=1e-11, atol=1e-13)
+    f = SO.fgmres(lambda v: A @ v, b, Ms, restart=30, rtol=1e-12)
+    assert f.iters == 1 and f.converged
+
+
+def test_bad_layouts_rejected():
+    me, A, b = _system(1, (6, 1, 1), 4, [M.PERIODIC], seed=1)
+    with pytest.raises(ValueError):
+        PC.time_slab_schwarz(A, 5, A.shape[0] // 4, 2)
+    with pytest.raises(ValueError):
+        PC.node_block_jacobi(5, A[:-1, :-1])

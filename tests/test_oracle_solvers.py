@@ -71,3 +71,76 @@ def test_bicgstab_equals_lu(d):
     x, it, rel, ok = SO.bicgstab(lambda v: A @ v, b, rtol=1e-13, maxiter=20000)
     assert ok and rel <= 1e-13 and it > 3
     assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) < 1e-10
+
+
+# ---- flexible GMRES ------------------------------------------------------------
+
+def test_fgmres_identity_is_gmres():
+    me, A, b = _system(d=2, nel=(6, 5, 1), nt=4)
+    Aop = lambda v: A @ v
+    g = SO.gmres(Aop, b, restart=7, rtol=1e-12, maxiter=5000)
+    f = SO.fgmres(Aop, b, None, restart=7, rtol=1e-12, maxiter=5000)
+    assert f.iters == g.iters and f.restarts == g.restarts
+    assert np.array_equal(f.x, g.x) and f.history == g.history
+
+
+def test_fgmres_exact_inverse_one_step():
+    me, A, b = _system(d=1, nel=(12, 1, 1), nt=6)
+    x_lu = SO.dense_solve(A, b)
+    f = SO.fgmres(lambda v: A @ v, b, lambda v: SO.dense_solve(A, v), restart=30, rtol=1e-12)
+    assert f.iters == 1 and f.converged
+    assert np.linalg.norm(f.x - x_lu) / np.linalg.norm(x_lu) < 1e-12
+
+
+def test_fgmres_fixed_preconditioner_is_right_preconditioned_gmres():
+    """x = M u with u the GMRES solution of (A M) u = b, M a fixed matrix."""
+    me, A, b = _system(d=1, nel=(14, 1, 1), nt=7, seed=3)
+    n = b.size
+    rng = np.random.default_rng(4)
+    Mm = np.eye(n) + 0.1 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    for k in (1, 4, 20):                   # k steps of one cycle: the same Krylov space M K_k(A M, b)
+        f = SO.fgmres(lambda v: A @ v, b, lambda v: Mm @ v, restart=k, rtol=1e-15, maxiter=k)
+        g = SO.gmres(lambda v: A @ (Mm @ v), b, restart=k, rtol=1e-15, maxiter=k)
+        assert f.iters == g.iters == k
+        np.testing.assert_allclose(f.history, g.history, rtol=1e-10)
+        assert np.linalg.norm(f.x - Mm @ g.x) / np.linalg.norm(f.x) < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8])
+def test_fgmres_varying_preconditioner_residual_identity(k):
+    """A preconditioner that differs at every call (alternating diagonal scalings and
+    a damped nonlinear map): after k steps of one cycle the implicit residual
+    |g_{k+1}| / ||b|| equals the true residual of x_0 + Z_k y_k."""
+    me, A, b = _system(d=1, nel=(10, 1, 1), nt=5, seed=5)
+    rng = np.random.default_rng(6)
+    D1 = rng.uniform(0.5, 2.0, b.size)
+    D2 = rng.uniform(0.5, 2.0, b.size)
+    calls = [0]
+
+    def M(v):
+        calls[0] += 1
+        if calls[0] % 3 == 0:
+            return v + 0.1 * np.tanh(np.abs(v)) * v
+        return (D1 if calls[0] % 3 == 1 else D2) * v
+
+    f = SO.fgmres(lambda v: A @ v, b, M, restart=k, rtol=1e-14, maxiter=k)
+    assert f.iters == k and calls[0] == k
+    assert abs(f.history[-1] - f.rel_resid_true) <= 1e-12 * max(1.0, f.rel_resid_true)
+    h = f.history
+    assert all(h[i + 1] <= h[i] + 1e-15 for i in range(len(h) - 1))
+
+
+def test_fgmres_varying_preconditioner_converges_to_lu():
+    me, A, b = _system(d=1, nel=(16, 1, 1), nt=12, seed=7)
+    x_lu = SO.dense_solve(A, b)
+    rng = np.random.default_rng(8)
+    D = [rng.uniform(0.5, 2.0, b.size) for _ in range(4)]
+    calls = [0]
+
+    def M(v):
+        calls[0] += 1
+        return D[calls[0] % 4] * v
+
+    f = SO.fgmres(lambda v: A @ v, b, M, restart=10, rtol=1e-12, maxiter=20000)
+    assert f.converged and f.rel_resid_true <= 1e-12
+    assert np.linalg.norm(f.x - x_lu) / np.linalg.norm(x_lu) < 1e-9
