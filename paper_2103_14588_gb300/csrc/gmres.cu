@@ -800,14 +800,17 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     sv.ortho = o.ortho;
     int rc = setup_workspace(mesh, o.method == 1 ? std::max(o.restart, 5) : o.restart, mixed, sv.w);
     if (rc) return rc;
-    static thread_local double *pinned = nullptr;
-    if (!pinned) {
+    // the mesh owns its page-locked record buffer (freed with the mesh), so
+    // solves from short-lived threads leave no pinned memory behind
+    if (!mesh->host_pinned) {
         const size_t nd = 8 * DST_MAX_VEC + 16 + (size_t)COL_STRIDE * DST_MAX_VEC;
-        if (cudaMallocHost(&pinned, sizeof(double) * nd) != cudaSuccess) {
-            pinned = nullptr;
+        if (cudaMallocHost(&mesh->host_pinned, sizeof(double) * nd) != cudaSuccess) {
+            cudaGetLastError();
+            mesh->host_pinned = nullptr;
             return DST_ERR_OOM;
         }
     }
+    double *pinned = mesh->host_pinned;
     sv.w.host = pinned;
     sv.w.host_cols = pinned + 8 * DST_MAX_VEC + 16;
     // first solve on this mesh: pick the apply tile shapes (the basis storage,

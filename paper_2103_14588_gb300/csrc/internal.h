@@ -81,6 +81,7 @@ struct dst_mesh {
     // GMRES workspace (allocated lazily by dst_solve)
     void *ws;
     size_t ws_bytes;
+    double *host_pinned;          // page-locked host copy of the per-step records (lazily, by dst_solve)
 };
 
 OpParams dst_internal_params(const dst_mesh *mesh);

@@ -209,6 +209,7 @@ extern "C" int dst_create_mesh(int d, const int64_t n_el[4], const double lo[4],
     m->d_V = nullptr;
     m->d_psi0 = nullptr;
     m->ws = nullptr;
+    m->host_pinned = nullptr;
     m->tile_variant[0] = m->tile_variant[1] = 0;
     m->tuned = false;
     m->ws_bytes = 0;
@@ -234,6 +235,7 @@ extern "C" int dst_destroy_mesh(dst_mesh *mesh) {
     cudaFree(mesh->d_V);
     cudaFree(mesh->d_psi0);
     cudaFree(mesh->ws);
+    if (mesh->host_pinned) cudaFreeHost(mesh->host_pinned);
     cudaSetDevice(dev_prev);
     delete mesh;
     return DST_OK;
