@@ -10,17 +10,37 @@ each returning a callable v -> M v for ``solvers.fgmres``:
   layers, each slab extended by ``overlap`` layers on both sides and solved
   exactly by sparse LU, its result kept on the slab's own layers only;
   overlap 0 is time-slab block Jacobi.
+* ``crank_nicolson_sweep``: a time-marching preconditioner built from the
+  structure of Eq. 7's discretisation.  Row t of D_w22 tests against the hat
+  function of time node t, which is the sum of its halves on the elements
+  (t-1, t) and (t, t+1).  Testing each time element against a constant
+  instead gives Crank-Nicolson: the block lower-bidiagonal
+      B[t, t] = i M_s + (h_t/2) K_s,   B[t, t-1] = -i M_s + (h_t/2) K_s,
+  with M_s the spatial mass matrix and K_s the spatial part of the operator
+  (for a time-independent operator, D_w22[t, t+-1] = +-(i/2) M_s +
+  (h_t/6) K_s on interior layers).  Averaging adjacent element rows,
+  S = (I + U) / 2 (U the shift to the next layer; the last layer, whose test
+  function is a half hat, keeps 1/2 only), reproduces the time-derivative
+  terms of D_w22 exactly and its spatial terms up to (h_t/12) K_s times the
+  second difference in time (and h_t/12 K_s (x_N - x_{N-1}) on the last
+  layer).  The preconditioner is M = B^-1 S^-1: a backward sweep for S and a
+  forward Crank-Nicolson march for B, one spatial solve per layer.
 
 The unknown vector is ordered [t][z][y][x][c] (time slowest), so a time
 layer is a contiguous run of ``per`` = n_spatial_nodes * NC entries and a
 node a run of NC entries.
 
 Only ``tests/`` imports this module.  Pinned by tests/test_oracle_precond.py:
-each preconditioner is the exact inverse of a matrix that is block diagonal
-in its own blocks, and one slab covering all layers inverts A.
+each Jacobi / Schwarz preconditioner is the exact inverse of a matrix that
+is block diagonal in its own blocks, and one slab covering all layers
+inverts A; for the Crank-Nicolson sweep, the extracted M_s is the real
+symmetric positive definite mass matrix (its entries sum to the domain
+volume times NC), h_t K_s is Hermitian, S B agrees with D_w22 on every row but
+the last for data linear in time, and M inverts S B.
 """
 
 import numpy as np
+import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 
@@ -61,3 +81,37 @@ def time_slab_schwarz(A, nt, per, S, overlap=0):
             z[own[0]:own[1]] = zs[own[0] - lo:own[1] - lo]
         return z
     return apply
+
+
+def crank_nicolson_sweep(A, nt, per):
+    """(apply, S, B, M_s, h_t K_s): v -> B^-1 S^-1 v for a time-independent D_w22
+    with ``nt`` >= 3 layers of ``per`` unknowns; M_s and K_s are taken from
+    layer 1's couplings to layers 0 and 2."""
+    A = A.tocsr()
+    if nt < 3 or A.shape[0] != nt * per:
+        raise ValueError("needs at least three time layers")
+
+    def block(t, u):
+        return A[t * per:(t + 1) * per, u * per:(u + 1) * per]
+
+    up, down = block(1, 2), block(1, 0)
+    Ms = (-1j * (up - down)).real.tocsr()                  # (i/2) M_s - (-(i/2) M_s) = i M_s
+    htK = (3.0 * (up + down)).tocsr()                       # 2 (h_t/6) K_s * 3 = h_t K_s
+    Bd = (1j * Ms + 0.5 * htK).tocsr()
+    Bl = (-1j * Ms + 0.5 * htK).tocsr()
+    B = sp.lil_matrix(A.shape, dtype=np.complex128)
+    S = sp.lil_matrix(A.shape, dtype=np.complex128)
+    eye = sp.eye(per, format="csr")
+    for t in range(nt):
+        B[t * per:(t + 1) * per, t * per:(t + 1) * per] = Bd
+        S[t * per:(t + 1) * per, t * per:(t + 1) * per] = 0.5 * eye
+        if t > 0:
+            B[t * per:(t + 1) * per, (t - 1) * per:t * per] = Bl
+        if t < nt - 1:
+            S[t * per:(t + 1) * per, (t + 1) * per:(t + 2) * per] = 0.5 * eye
+    B, S = B.tocsc(), S.tocsc()
+    Blu, Slu = spla.splu(B), spla.splu(S)
+
+    def apply(v):
+        return Blu.solve(Slu.solve(np.asarray(v, dtype=np.complex128)))
+    return apply, S, B, Ms, htK

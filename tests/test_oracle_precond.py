@@ -73,3 +73,57 @@ def test_bad_layouts_rejected():
         PC.time_slab_schwarz(A, 5, A.shape[0] // 4, 2)
     with pytest.raises(ValueError):
         PC.node_block_jacobi(5, A[:-1, :-1])
+
+
+# ---- Crank-Nicolson sweep ------------------------------------------------------
+
+def _open_end_nodes(me):
+    """Boolean per unknown entry: the node lies at an end of an open axis."""
+    idx = np.indices((me.nu[2], me.nu[1], me.nu[0]))          # z, y, x
+    end = np.zeros(idx.shape[1:], dtype=bool)
+    for k in range(me.d):
+        if me.bc[k] == M.OPEN:
+            i = idx[2 - k]
+            end |= (i == 0) | (i == me.nu[k] - 1)
+    return np.repeat(end.ravel(), me.nc)
+
+
+@pytest.mark.parametrize("d,nel,bc", [(1, (12, 1, 1), [M.PERIODIC]), (2, (5, 4, 1), [M.OPEN, M.PERIODIC]),
+                                      (2, (6, 4, 1), [M.DIRICHLET, M.PERIODIC]),
+                                      (3, (3, 4, 3), [M.PERIODIC, M.PERIODIC, M.OPEN])])
+def test_crank_nicolson_sweep_blocks(d, nel, bc):
+    nt = 5
+    me, A, b = _system(d, nel, nt, bc, seed=20 + d)
+    per = me.n_spatial_nodes * me.nc
+    Mc, S, B, Ms, htK = PC.crank_nicolson_sweep(A, nt, per)
+    # the mass matrix: real symmetric positive definite, entries summing to the volume per component
+    Md = Ms.toarray()
+    np.testing.assert_allclose(Md, Md.T, rtol=0, atol=1e-15)
+    assert np.linalg.eigvalsh(Md).min() > 0
+    if M.DIRICHLET not in bc:                    # the unknown hats sum to one on the whole domain
+        vol = np.prod([me.hi[k] - me.lo[k] for k in range(d)])
+        assert Md.sum() == pytest.approx(vol * me.nc, rel=1e-12)
+    # the spatial part is Hermitian but for the outflow term of open axes, which
+    # couples end nodes only
+    Kd = htK.toarray()
+    end = _open_end_nodes(me)
+    skew = np.abs(Kd - Kd.conj().T)
+    assert skew[~end, :].max(initial=0) <= 1e-14 and skew[:, ~end].max(initial=0) <= 1e-14
+    assert (skew.max() > 1e-6) == (M.OPEN in bc)
+    # data linear in time: S B equals D_w22 except on the last layer, where the
+    # difference is (h_t / 12) K_s times the step c
+    rng = np.random.default_rng(d)
+    c = rng.standard_normal(per) + 1j * rng.standard_normal(per)
+    x = np.concatenate([(t + 1) * c for t in range(nt)])
+    diff = A @ x - S @ (B @ x)
+    assert np.abs(diff[:-per]).max() <= 1e-12 * np.abs(A @ x).max()
+    np.testing.assert_allclose(diff[-per:], htK @ c / 12, rtol=1e-10, atol=1e-13)
+    # the preconditioner inverts S B (backward sweep for S, then the forward march)
+    y = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    np.testing.assert_allclose(S @ (B @ Mc(y)), y, rtol=0, atol=1e-10 * np.abs(y).max())
+
+
+def test_crank_nicolson_sweep_needs_three_layers():
+    me, A, b = _system(1, (6, 1, 1), 2, [M.PERIODIC], seed=1)
+    with pytest.raises(ValueError):
+        PC.crank_nicolson_sweep(A, 2, A.shape[0] // 2)
