@@ -1,6 +1,6 @@
 """Preconditioners for flexible GMRES on A Psi_u = b (test infrastructure).
 
-The paper's conclusion asks for a preconditioner (suggesting a time-additive
+The paper's conclusion (Sec. 5) asks for a preconditioner (suggesting a time-additive
 Schwarz method) and specifies none.  These are the non-learned candidates,
 each returning a callable v -> M v for ``solvers.fgmres``:
 

@@ -1,6 +1,6 @@
 """Convolutional U-Net for a learned right preconditioner (test infrastructure).
 
-The paper's conclusion asks for a preconditioner and specifies none; this is
+The paper's conclusion (Sec. 5) asks for a preconditioner and specifies none; this is
 a learned candidate for flexible GMRES: a network M that maps a residual r
 (the unknown vector, layout [t][z][y][x][c]) to a correction close to
 A^-1 r.  It has no counterpart in the paper; the definitions below are the
