@@ -127,3 +127,45 @@ def test_crank_nicolson_sweep_needs_three_layers():
     me, A, b = _system(1, (6, 1, 1), 2, [M.PERIODIC], seed=1)
     with pytest.raises(ValueError):
         PC.crank_nicolson_sweep(A, 2, A.shape[0] // 2)
+
+
+@pytest.mark.parametrize("d,nel,V", [(1, (16, 1, 1), 0.0), (2, (8, 6, 1), 0.7)])
+def test_crank_nicolson_sweep_is_one_scan_per_frequency_on_periodic_meshes(d, nel, V):
+    """Periodic axes and a constant potential make M_s and K_s block circulant, so
+    the spatial FFT turns the sweep into an independent scan over t per frequency:
+    x^_t = (i M^ + (h_t/2) K^)^-1 (s^_t - (-i M^ + (h_t/2) K^) x^_{t-1}) after the
+    backward scan s_t = 2 v_t - s_{t+1} (s_N = 2 v_N).  Written here from those
+    recurrences alone and compared with the oracle's sparse-LU sweep."""
+    nt = 6
+    rng = np.random.default_rng(30 + d)
+    me = M.Mesh(d, list(nel) + [nt], [0, 0, 0, 0], [1.0, 1.3, 1.0, 0.6], [M.PERIODIC] * 3)
+    psi0 = rng.standard_normal(me.spatial_shape) + 1j * rng.standard_normal(me.spatial_shape)
+    A, _ = OP.split(me, OP.assemble(me, 1.0, np.full(me.nel[0] * me.nel[1] * me.nel[2], V)), psi0)
+    A = A.tocsr()
+    nc, grid = me.nc, (me.nu[1], me.nu[0])                  # (n_y, n_x)
+    per = me.n_spatial_nodes * nc
+    Mc, S, B, Ms, htK = PC.crank_nicolson_sweep(A, nt, per)
+
+    def symbol(op):
+        """NC x NC symbol per frequency of a block-circulant layer operator: the FFT of
+        its first block row, with the sign of a correlation (column offset j)."""
+        row = op[:nc, :].toarray().reshape(nc, grid[0], grid[1], nc)   # [c_out, y, x, c_in]
+        # (op u)_0 = sum_j row_j u_j; for u_j = e^{i k j} u this is sum_j row_j e^{i k j}
+        return np.fft.ifft2(row, axes=(1, 2)).transpose(1, 2, 0, 3) * grid[0] * grid[1]
+
+    Mh, Kh = symbol(Ms.tocsr()), symbol(htK.tocsr())
+    Bd = 1j * Mh + 0.5 * Kh
+    Bl = -1j * Mh + 0.5 * Kh
+    v = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    vt = v.reshape(nt, grid[0], grid[1], nc)
+    s = np.zeros_like(vt)
+    s[-1] = 2 * vt[-1]
+    for t in range(nt - 2, -1, -1):                           # S^-1: s_t = 2 v_t - s_{t+1}
+        s[t] = 2 * vt[t] - s[t + 1]
+    sh = np.fft.fft2(s, axes=(1, 2))
+    xh = np.zeros_like(sh)
+    for t in range(nt):                                       # B^-1: the forward march per frequency
+        rhs = sh[t] - (np.einsum("yxab,yxb->yxa", Bl, xh[t - 1]) if t > 0 else 0)
+        xh[t] = np.linalg.solve(Bd, rhs[..., None])[..., 0]
+    x = np.fft.ifft2(xh, axes=(1, 2)).ravel()
+    np.testing.assert_allclose(x, Mc(v), rtol=0, atol=1e-10 * np.abs(x).max())
