@@ -18,10 +18,15 @@ Three routes, all from the same element operator (oracle.element):
 Potential V: one value per spatial element (sampled at its centroid), constant
 in time, entering the element operator as -V_e D^0 (x) I (Hamiltonian form).
 
+Nonzero Dirichlet values (``split(..., boundary=...)``) move to the
+right-hand side with the t = 0 layer; the paper's Eq. 2 prescribes the
+boundary values, and every workload here uses zero.
+
 Pinned by tests/test_oracle_operator.py: the exact discrete Fourier reduction
 of a periodic mesh (symbols h(2 + cos th)/3 and i sin th), exact reduction of
 2+1 / 3+1 with data uniform in y (and z) to 1+1, equality of the three routes,
-and identical LU solutions of the Hamiltonian and appendix forms.
+identical LU solutions of the Hamiltonian and appendix forms, and Dirichlet
+data taken from an open-axis solution reproducing that solution inside.
 """
 
 import numpy as np
@@ -167,12 +172,33 @@ def assemble(mesh, m, V, form="hamiltonian"):
     return Dw
 
 
-def split(mesh, Dw, psi0):
-    """Eq. 11: return (D_w22, b = -D_w21 Psi_known) with Psi_known the t = 0 layer."""
+def dirichlet_end_mask(mesh):
+    """Boolean spatial geometric array (gz, gy, gx): True at the end nodes of Dirichlet axes."""
+    msk = np.zeros(mesh.geo_shape[1:4], dtype=bool)
+    for k in range(mesh.d):
+        if mesh.bc[k] == 2:                                   # DIRICHLET
+            sl = [slice(None)] * 3
+            for end in (0, mesh.ngeo[k] - 1):
+                sl[2 - k] = end
+                msk[tuple(sl)] = True
+    return msk
+
+
+def split(mesh, Dw, psi0, boundary=None):
+    """Eq. 11: return (D_w22, b = -D_w21 Psi_known).
+
+    Psi_known is the t = 0 layer (psi0 on its unknown spatial nodes) and the
+    end nodes of Dirichlet axes on every layer, zero unless ``boundary`` (a
+    geometric array of shape mesh.geo_shape) gives their spinors; its other
+    entries are ignored.  Prescribed Dirichlet values thus enter only the
+    right-hand side, like the initial data."""
     nc = mesh.nc
     unk = np.repeat(mesh.unknown_mask_geo().ravel(), nc)
     known_vals = np.zeros(mesh.geo_shape, dtype=np.complex128)
     known_vals[0] = mesh.layer_to_geo(psi0)
+    if boundary is not None:
+        ends = dirichlet_end_mask(mesh)
+        known_vals[:, ends] = np.asarray(boundary, dtype=np.complex128).reshape(mesh.geo_shape)[:, ends]
     known_vals = known_vals.ravel()[~unk]
     D22 = Dw[unk][:, unk].tocsr()
     D21 = Dw[unk][:, ~unk].tocsr()

@@ -174,3 +174,35 @@ def test_potential_is_minus_V_mass():
     Mm = mass[unk][:, unk].toarray()
     assert np.allclose(Mm, Mm.T)
     assert np.all(np.linalg.eigvalsh(Mm.real) > 0)
+
+
+@pytest.mark.parametrize("d,nel,bc_other", [(1, (14, 1, 1), None), (2, (10, 4, 1), M.PERIODIC)])
+def test_dirichlet_data_from_an_open_solution(d, nel, bc_other):
+    """The interior rows of a Dirichlet problem are the interior rows of the open
+    problem on the same mesh, with the end-node values moved to the right-hand
+    side.  So Dirichlet data equal to an open-axis solution's end values (and its
+    initial layer) gives back that solution at every interior node, exactly."""
+    from oracle import solvers as SO
+    nt = 5
+    rng = np.random.default_rng(40 + d)
+    lo, hi = [-1.0, 0.0, 0.0, 0.0], [1.5, 1.0, 1.0, 0.8]
+    rest = [bc_other] if d == 2 else []
+    mo = M.Mesh(d, list(nel) + [nt], lo, hi, [M.OPEN] + rest)
+    md = M.Mesh(d, list(nel) + [nt], lo, hi, [M.DIRICHLET] + rest)
+    V = rng.uniform(-0.5, 1.0, nel[0] * nel[1] * nel[2])
+    psi0_open = rng.standard_normal(mo.spatial_shape) + 1j * rng.standard_normal(mo.spatial_shape)
+    Ao, bo = OP.split(mo, OP.assemble(mo, 0.8, V), psi0_open)
+    xo = SO.dense_solve(Ao, bo)
+    go = mo.to_geo(xo)                                 # open solution on every geometric node,
+    go[0] = mo.layer_to_geo(psi0_open)                 # its initial layer included
+    # same geometry: the open mesh's nodes are the Dirichlet mesh's geometric nodes
+    assert mo.geo_shape == md.geo_shape
+    inner = tuple(slice(md.u0[k], md.u0[k] + md.nu[k]) for k in (2, 1, 0))
+    psi0_d = go[0][inner]                              # the initial layer on the Dirichlet unknowns
+    Ad, bd = OP.split(md, OP.assemble(md, 0.8, V), psi0_d, boundary=go)
+    xd = SO.dense_solve(Ad, bd)
+    np.testing.assert_allclose(xd, md.from_geo(go).ravel(), rtol=0, atol=1e-11 * np.abs(xo).max())
+    # without the boundary data the homogeneous problem is solved instead
+    A0, b0 = OP.split(md, OP.assemble(md, 0.8, V), psi0_d)
+    assert np.array_equal(A0.toarray(), Ad.toarray())
+    assert np.linalg.norm(SO.dense_solve(A0, b0) - xd) > 1e-3 * np.linalg.norm(xd)
