@@ -15,7 +15,7 @@
 * ``zb_frequency``: the Zitterbewegung angular frequency 2E of the
   oscillating term of Eq. 18.
 
-Pinned by tests/test_oracle_exact.py: the plane wave satisfies the PDE;
+Pinned by tests/test_oracle_physics.py: the plane wave satisfies the PDE;
 evolve_fft agrees with plane_wave on single modes and conserves the norm;
 matching agrees with the transfer integration for a steep step and with the
 textbook step formula; Eq. 24 (as read) agrees with the transfer integration.

@@ -14,8 +14,14 @@ Trapezoid weights per axis: periodic axes weight every node by h; open axes
 halve the two end nodes; Dirichlet axes hold interior nodes only (the ends are
 zero) and weight them by h.
 
-Pinned by tests/test_oracle_exact.py (charge of a normalised packet, <x> of
-a shifted symmetric packet, T + R = 1).
+Pinned by tests/test_oracle_observables.py: the charge of densities for
+which the trapezoid rule is exact equals their closed-form integral; a
+one-node density has its mean position at that node on every axis of a 3+1
+mesh; transmitted shares follow the node weights (a node at x0 counting
+half); a periodic-grid plane wave u_+-(p) e^{i p.x} has energy +-E(p) times
+the volume, and a superposition of modes the sum of its parts.  The charge
+self-convergence and Zitterbewegung tests (tests/test_oracle_physics.py) use
+charge and mean_position on FEM solutions.
 """
 
 import numpy as np
@@ -75,7 +81,6 @@ def energy(mesh, psi_layers, m):
     d = mesh.d
     al, be = alphas_beta(d)
     out = []
-    axes = tuple(range(1, 1 + 3))
     for psi in psi_layers:
         F = np.fft.fftn(psi, axes=(0, 1, 2))
         ks = []
@@ -89,5 +94,4 @@ def energy(mesh, psi_layers, m):
             HF = HF + p[k][..., None] * np.einsum("ab,zyxb->zyxa", al[k], F)
         Hpsi = np.fft.ifftn(HF, axes=(0, 1, 2))
         out.append(np.real(np.sum(np.conj(psi) * Hpsi) * np.prod([mesh.h[k] for k in range(d)])))
-    del axes
     return np.array(out)

@@ -140,3 +140,38 @@ def test_transmission_shares():
     r[0] = 1.0
     T, _ = OB.transmission(mesh, _layers(mesh, [r], nlayers=1)[0], LO[0] + 0.2)
     assert T == pytest.approx(1.0, abs=1e-15)
+
+
+def _plane(mesh, j, u):
+    """u e^{i p.x} on the unknown nodes, p_k = 2 pi j_k / L_k (a mode of the periodic grid)."""
+    p = np.array([2 * np.pi * j[k] / (mesh.hi[k] - mesh.lo[k]) for k in range(mesh.d)])
+    phase = np.zeros((mesh.nu[2], mesh.nu[1], mesh.nu[0]))
+    for k in range(mesh.d):
+        shape = [1, 1, 1]
+        shape[2 - k] = -1
+        phase = phase + p[k] * mesh.node_coords(k).reshape(shape)
+    return np.exp(1j * phase)[..., None] * u, p
+
+
+@pytest.mark.parametrize("d,n_el,j", [(1, [16], [3]), (2, [12, 10], [2, -3]), (3, [8, 6, 10], [1, 2, -2])])
+def test_energy_of_plane_waves(d, n_el, j):
+    """A periodic-grid plane wave u_+-(p) e^{i p.x} has energy +-E(p) x volume, E = sqrt(p^2 + m^2);
+    a superposition of two modes has the sum of the parts (the modes are orthogonal)."""
+    import workloads as W
+    m = 1.3
+    mesh = _mesh(d, n_el, [PERIODIC] * d)
+    vol = np.prod([mesh.hi[k] - mesh.lo[k] for k in range(d)])
+    psi_p, p = _plane(mesh, j, 1.0)
+    up, um = W.spinor_pm(d, p, m)
+    E = np.sqrt(p @ p + m * m)
+    for u, sign in ((up, 1.0), (um, -1.0)):
+        psi, _ = _plane(mesh, j, u)
+        assert OB.energy(mesh, psi[None], m)[0] == pytest.approx(sign * E * vol, rel=1e-12)
+    j2 = [-x + 1 for x in j]
+    psi2, p2 = _plane(mesh, j2, 1.0)
+    up2, um2 = W.spinor_pm(d, p2, m)
+    E2 = np.sqrt(p2 @ p2 + m * m)
+    a, c = 0.6 - 0.2j, 0.5j
+    mix = a * _plane(mesh, j, up)[0] + c * _plane(mesh, j2, um2)[0]
+    expect = (abs(a) ** 2 * E - abs(c) ** 2 * E2) * vol
+    assert OB.energy(mesh, mix[None], m)[0] == pytest.approx(expect, rel=1e-12)
