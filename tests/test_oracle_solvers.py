@@ -144,3 +144,19 @@ def test_fgmres_varying_preconditioner_converges_to_lu():
     f = SO.fgmres(lambda v: A @ v, b, M, restart=10, rtol=1e-12, maxiter=20000)
     assert f.converged and f.rel_resid_true <= 1e-12
     assert np.linalg.norm(f.x - x_lu) / np.linalg.norm(x_lu) < 1e-9
+
+
+def test_iteration_count_generator_agrees_with_the_assembled_solve():
+    """oracle/iteration_counts.py counts GMRES(30) steps through the matrix-free
+    apply and right-hand side; on the 64 x 64 plane wave that route and the
+    assembled D_w22 both converge, in step counts a few percent apart (994 and
+    978): over ~1000 restarted steps the summation order alone moves the count."""
+    import workloads as W
+    from oracle import iteration_counts as IC
+    rec = IC.count("plane_wave_1p1")
+    w = W.plane_wave_1p1()
+    me = M.Mesh(w.d, w.n_el, w.lo, w.hi, w.bc)
+    A, b = OP.split(me, OP.assemble(me, w.m, w.V), w.psi0)
+    ref = SO.gmres(lambda v: A @ v, b, restart=IC.RESTART, rtol=IC.RTOL, maxiter=20000)
+    assert rec["converged"] and ref.converged and rec["restart"] == 30 and rec["rtol"] == 1e-8
+    assert abs(rec["iters"] - ref.iters) <= 0.03 * ref.iters and rec["rel_resid_true"] <= 1e-8
