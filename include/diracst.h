@@ -115,6 +115,26 @@ DST_API int dst_set_potential(dst_mesh *mesh, const double *V_elem);
 DST_API int dst_set_initial_data(dst_mesh *mesh, const double *psi0);
 
 /*
+ * Prescribed spinors on Dirichlet walls (Sec. 2.1, Eq. 2: Psi = Psi_0 on the
+ * boundary of the domain).  Like the t = 0 layer they are known, so the split
+ * of Eq. 11 moves them to the right-hand side: from this call on,
+ * dst_build_rhs and dst_solve add -D_w[unknowns, wall nodes] Psi_wall over
+ * every time layer to b.  psi_bd is HOST memory with the spinors of time
+ * layers t = 0..N_t on the full node grid of each layer, the walls included:
+ * (N_t + 1) layers of gz x gy x gx nodes of NC complex values (2 doubles
+ * each), layer slowest, then z, y, x, component, where gk = n_el on a
+ * periodic axis, n_el + 1 on an open or Dirichlet axis (axes the mesh does not
+ * have count 1).  Only the end nodes of Dirichlet axes are read (layer 0's
+ * included; the rest of layer 0 comes from dst_set_initial_data); all other
+ * entries are ignored.  The mesh keeps a device copy.  NULL restores
+ * homogeneous walls (the default).  Errors: DST_ERR_ARG (mesh without a
+ * Dirichlet axis, non-finite wall value; the previous data stays), DST_ERR_OOM,
+ * DST_ERR_CUDA.  dst_build_rhs then also needs stream-ordered scratch of two
+ * vectors of the open-wall grid (DST_ERR_OOM if it cannot get it).
+ */
+DST_API int dst_set_boundary_data(dst_mesh *mesh, const double *psi_bd);
+
+/*
  * Right-hand side b = -D_w21 Psi_0 (Sec. 2.1, Eq. 11; Algorithm 1 step 5)
  * into the caller's DEVICE FP64 vector b (n_unknowns complex).  Only the
  * first unknown time layer is non-zero; the call writes every entry.
@@ -325,6 +345,28 @@ DST_API int dst_solve_batch(int count, dst_mesh *const *meshes, const dst_solve_
  * h with the two end nodes halved (open axes).  Deterministic (fixed order).
  */
 DST_API int dst_observables(const dst_mesh *mesh, const void *psi, double x0, void *out, void *stream);
+
+/*
+ * Testing hooks.  The paper has no counterpart: these make the library's
+ * failure paths reachable from a test on a healthy GPU, with nothing faulted.
+ * Process-wide settings, meant for tests only.
+ *   DST_TEST_WAIT_LIMIT  value = tries a bulk-copy wait of the Arnoldi
+ *                        projection makes before giving up; -1 restores the
+ *                        standard 2^22.  With 0 every wait gives up at once,
+ *                        before its copy can have landed: the kernel stops
+ *                        consuming, waits (standard limit) for the copies it
+ *                        has in flight, flags the step, and dst_solve returns
+ *                        DST_ERR_CUDA naming the wait in dst_last_error_detail().
+ *                        Only mixed solves on an FP32-stored basis of at least
+ *                        4,000,000 unknowns use that kernel.
+ *   DST_TEST_FAIL_ALLOC  value = how many of the following GMRES workspace
+ *                        allocations fail as if the device were out of memory
+ *                        (dst_solve returns DST_ERR_OOM, the mesh stays usable);
+ *                        0 clears.
+ * Errors: DST_ERR_ARG for an unknown hook or a value out of range.
+ */
+enum { DST_TEST_WAIT_LIMIT = 1, DST_TEST_FAIL_ALLOC = 2 };
+DST_API int dst_testing_set(int hook, int64_t value);
 
 /* Static, human-readable name of a status code. */
 DST_API const char *dst_status_string(int status);

@@ -20,13 +20,15 @@ DST_OK, DST_NOT_CONVERGED = 0, 1
 DST_ERR_ARG, DST_ERR_OOM, DST_ERR_CUDA, DST_ERR_NAN, DST_ERR_STATE = -1, -2, -3, -5, -6
 DST_BC_PERIODIC, DST_BC_OPEN, DST_BC_DIRICHLET = 0, 1, 2
 DST_FP64, DST_FP32 = 0, 1
+DST_TEST_WAIT_LIMIT, DST_TEST_FAIL_ALLOC = 1, 2
 
 EXPORTED = (
     "dst_create_mesh", "dst_destroy_mesh", "dst_mesh_sizes", "dst_set_mass", "dst_set_potential",
     "dst_set_initial_data", "dst_build_rhs", "dst_apply_operator", "dst_arnoldi_project",
     "dst_arnoldi_update", "dst_default_solve_opts", "dst_solve", "dst_status_string",
     "dst_last_error_detail", "dst_arnoldi_project_noalloc", "dst_observables", "dst_solve_batch",
-    "dst_tune_apply", "dst_set_apply_variant", "dst_get_apply_variant",
+    "dst_tune_apply", "dst_set_apply_variant", "dst_get_apply_variant", "dst_testing_set",
+    "dst_set_boundary_data",
 )
 
 
@@ -80,6 +82,7 @@ def _load():
         "dst_set_mass": (c_int, [vp, c_double]),
         "dst_set_potential": (c_int, [vp, vp]),
         "dst_set_initial_data": (c_int, [vp, vp]),
+        "dst_set_boundary_data": (c_int, [vp, vp]),
         "dst_build_rhs": (c_int, [vp, vp, vp]),
         "dst_apply_operator": (c_int, [vp, c_int, vp, vp, vp]),
         "dst_arnoldi_project": (c_int, [i64, c_int, vp, vp, vp, vp]),
@@ -94,6 +97,7 @@ def _load():
         "dst_get_apply_variant": (c_int, [vp, c_int, P(c_int), P(c_int)]),
         "dst_status_string": (ctypes.c_char_p, [c_int]),
         "dst_last_error_detail": (ctypes.c_char_p, []),
+        "dst_testing_set": (c_int, [c_int, i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -202,6 +206,17 @@ def dst_set_initial_data(mesh, psi0):
     return _check(_lib.dst_set_initial_data(mesh, arr.ctypes.data), "dst_set_initial_data")
 
 
+def dst_set_boundary_data(mesh, psi_bd, n_values=None):
+    """psi_bd: host complex128 array of the wall spinors on every layer's full node grid
+    ((N_t + 1) x gz x gy x gx x NC, Dirichlet axes with both end nodes), or None."""
+    if psi_bd is None:
+        return _check(_lib.dst_set_boundary_data(mesh, None), "dst_set_boundary_data")
+    arr = np.ascontiguousarray(psi_bd, dtype=np.complex128).ravel()
+    if n_values is not None and arr.size != n_values:
+        raise ValueError("psi_bd needs %d complex values, got %d" % (n_values, arr.size))
+    return _check(_lib.dst_set_boundary_data(mesh, arr.ctypes.data), "dst_set_boundary_data")
+
+
 def dst_build_rhs(mesh, b, stream=None):
     import torch
     _, nu, _ = dst_mesh_sizes(mesh)
@@ -256,6 +271,11 @@ def dst_observables(mesh, psi, x0, out, stream=None):
     pp = _dev_ptr(psi, torch.complex128, nu, "psi")
     po = _dev_ptr(out, torch.float64, 5 * nt, "out")
     return _check(_lib.dst_observables(mesh, pp, float(x0), po, _stream(stream, psi, out)), "dst_observables")
+
+
+def dst_testing_set(hook, value):
+    """Testing hook (DST_TEST_WAIT_LIMIT / DST_TEST_FAIL_ALLOC, see diracst.h)."""
+    return _check(_lib.dst_testing_set(int(hook), int(value)), "dst_testing_set")
 
 
 def dst_default_solve_opts():
@@ -337,6 +357,7 @@ class Mesh:
             if np.size(V) != ne:
                 raise ValueError("V needs one value per spatial element (%d), got %d" % (ne, np.size(V)))
         self.handle = None
+        self.d, self.n_el, self.bc = int(d), [int(v) for v in n_el], [int(v) for v in (list(bc) + [0, 0, 0])[:3]]
         self.handle = dst_create_mesh(d, n_el, lo, hi, bc)
         self.n_spatial, self.n_unknowns, self.ncomp = dst_mesh_sizes(self.handle)
         if m is not None:
@@ -349,6 +370,22 @@ class Mesh:
     @classmethod
     def from_workload(cls, w):
         return cls(w.d, w.n_el, w.lo, w.hi, w.bc, m=w.m, V=w.V, psi0=w.psi0)
+
+    def wall_grid_shape(self):
+        """Shape (N_t + 1, gz, gy, gx, NC) of the array dst_set_boundary_data reads."""
+        g = []
+        for k in range(3):
+            if k >= self.d:
+                g.append(1)
+            elif self.bc[k] == DST_BC_PERIODIC:
+                g.append(self.n_el[k])
+            else:
+                g.append(self.n_el[k] + 1)
+        return (self.n_el[3] + 1, g[2], g[1], g[0], self.ncomp)
+
+    def set_boundary_data(self, psi_bd):
+        n = None if psi_bd is None else int(np.prod(self.wall_grid_shape()))
+        return dst_set_boundary_data(self.handle, psi_bd, n)
 
     def close(self):
         if self.handle:

@@ -431,7 +431,9 @@ int dst_reduction_blocks(int64_t n) {
 // stream-ordered allocator.  Host code cannot pass the symbol itself (on the
 // host it only names a shadow variable); its device address is looked up once
 // per device with cudaGetSymbolAddress and cached.
-#define DST_NOALLOC_PARTIALS ((size_t)1216 * DST_MAX_VEC)   // >= DST_MAX_RED_BLOCKS * DST_MAX_VEC
+#define DST_NOALLOC_PARTIALS ((size_t)1216 * DST_MAX_VEC)
+static_assert(DST_NOALLOC_PARTIALS >= (size_t)DST_MAX_RED_BLOCKS * DST_MAX_VEC,
+              "the static scratch must hold the partials of the largest reduction grid for 64 vectors");
 static __device__ __align__(256) double2 g_noalloc_partials[DST_NOALLOC_PARTIALS];
 
 static std::mutex g_noalloc_mutex;
@@ -456,7 +458,14 @@ static int noalloc_scratch(void **out) {
 
 extern "C" int dst_arnoldi_project_noalloc(int64_t n, int nvec, const void *V, const void *w, void *h,
                                            void *stream) {
-    if (n < 1 || !V || !w || !h) return DST_ERR_ARG;
+    if (n < 1) {
+        dst_internal_set_error_detail("dst_arnoldi_project_noalloc: n must be at least 1");
+        return DST_ERR_ARG;
+    }
+    if (!V || !w || !h) {
+        dst_internal_set_error_detail("dst_arnoldi_project_noalloc: V, w and h must be device pointers, not NULL");
+        return DST_ERR_ARG;
+    }
     if (nvec < 1 || nvec > DST_MAX_VEC) {
         dst_internal_set_error_detail("dst_arnoldi_project_noalloc: nvec must be 1..64 (the static scratch "
                                       "holds 1216 x 64 partial sums)");

@@ -388,10 +388,21 @@ constexpr unsigned TMA_WAIT_LIMIT = 1u << 22;   // try_wait attempts before a wa
 
 constexpr int TMA_THREADS = DF_THREADS + 32;   // eight consumer warps and one producer warp
 
+// Failure handling.  A consumer warp that meets a failed wait (or sees that
+// another warp failed) stops consuming at once: it neither reads nor releases
+// that slot or any later one, and records how many copies it waited for.  A
+// copy is issued into a slot only after every consumer warp has released the
+// copy before it in that slot, and a warp releases only copies it waited for,
+// so at exit the copies that may still be in flight are exactly those from the
+// smallest completed-wait count over the consumer warps up to the last one
+// issued - at most one per slot, each the latest phase of its slot's full
+// mbarrier.  Thread 0 waits for each of them with the standard limit
+// (whatever limit the consumers used) before the CTA touches its results or
+// exits.  `wait_limit` bounds the consumers' and the producer's waits.
 __global__ void __launch_bounds__(TMA_THREADS, 2)
 project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const float2 *__restrict__ w,
                    double2 *__restrict__ partials, const double *gate, double2 *__restrict__ h,
-                   double *__restrict__ wnrm2, unsigned *__restrict__ ticket, double *err) {
+                   double *__restrict__ wnrm2, unsigned *__restrict__ ticket, double *err, unsigned wait_limit) {
     if (gate != nullptr && !(gate[0] < 0.5 * gate[3])) {           // DGKS: no second pass needed
         if (blockIdx.x == 0)
             for (int j = threadIdx.x; j < nvec; j += TMA_THREADS) h[j] = make_double2(0.0, 0.0);
@@ -403,7 +414,7 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
     extern __shared__ __align__(128) float4 ring[];  // TMA_SLOTS x U
     __shared__ __align__(8) uint64_t full[TMA_SLOTS], empty[TMA_SLOTS];
     __shared__ double red[NW][2 * DST_MAX_VEC + 1];
-    __shared__ int failed, s_issued, s_consumed;
+    __shared__ int failed, s_issued, s_done[NW];
     volatile int *vfailed = &failed;                 // polled across warps
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int64_t b, e;
@@ -419,7 +430,7 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
         }
         failed = 0;
         s_issued = 0;
-        s_consumed = 0;
+        for (int q = 0; q < NW; ++q) s_done[q] = 0;
         mbar_fence_init();
     }
     __syncthreads();
@@ -433,7 +444,7 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
             for (; k < K && !*vfailed; ++k) {
                 const int slot = k % TMA_SLOTS;
                 if (k >= TMA_SLOTS &&
-                    !mbar_wait_bounded(&empty[slot], (unsigned)(((k / TMA_SLOTS) - 1) & 1), TMA_WAIT_LIMIT)) {
+                    !mbar_wait_bounded(&empty[slot], (unsigned)(((k / TMA_SLOTS) - 1) & 1), wait_limit)) {
                     *vfailed = 1;
                     break;
                 }
@@ -452,11 +463,17 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
             s_issued = k;
         }
     } else {
-        int k = 0;                                   // next copy to consume
-        auto wait_item = [&]() {
+        int k = 0;                                   // copies this warp waited for (and released)
+        // warp-uniform: the slot of copy k, or nullptr once a wait failed here or elsewhere
+        auto wait_item = [&]() -> const float4 * {
             const int slot = k % TMA_SLOTS;
-            if (!*vfailed && !mbar_wait_bounded(&full[slot], (unsigned)((k / TMA_SLOTS) & 1), TMA_WAIT_LIMIT))
-                *vfailed = 1;
+            bool ok = __shfl_sync(0xffffffffu, *vfailed == 0 ? 1 : 0, 0) != 0;
+            if (ok) ok = mbar_wait_bounded(&full[slot], (unsigned)((k / TMA_SLOTS) & 1), wait_limit);
+            ok = __all_sync(0xffffffffu, ok) != 0;
+            if (!ok) {
+                if (lane == 0) *vfailed = 1;
+                return nullptr;
+            }
             return (const float4 *)(ring + (size_t)slot * U);
         };
         auto release_item = [&]() {
@@ -464,18 +481,20 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
             if (lane == 0) mbar_arrive(&empty[k % TMA_SLOTS]);
             ++k;
         };
-        for (int g = 0; g < ngr && !*vfailed; ++g) {
+        bool stop = false;
+        for (int g = 0; g < ngr && !stop; ++g) {
             const int gv = nvec - 4 * g < 4 ? nvec - 4 * g : 4;
             DfAcc R[4], I[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) { R[q].zero(); I[q].zero(); }
-            for (int c = 0; c < nch; ++c) {
+            for (int c = 0; c < nch && !stop; ++c) {
                 const int64_t c0 = b + (int64_t)c * TMA_CHUNK;
                 const int units = (int)(((e - c0 < TMA_CHUNK) ? e - c0 : TMA_CHUNK) >> 1);
                 float4 a[UPT];
                 float bound = 0.f;
                 {
                     const float4 *sw4 = wait_item();
+                    if (!sw4) { stop = true; break; }
 #pragma unroll
                     for (int i = 0; i < UPT; ++i) {
                         const int u = tid + i * DF_THREADS;
@@ -494,6 +513,7 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
                 const float sigma = anchor_above(bound);
                 for (int q = 0; q < gv; ++q) {
                     const float4 *sv = wait_item();
+                    if (!sv) { stop = true; break; }
                     AnAcc re, im;
                     re.init(sigma);
                     im.init(sigma);
@@ -511,6 +531,7 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
                     release_item();
                 }
             }
+            if (stop) break;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (q < gv) {
@@ -519,13 +540,17 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
                 }
             }
         }
-        if (tid == 0) s_consumed = k;
+        if (lane == 0) s_done[warp] = k;
     }
     __syncthreads();
-    // a failed wait can leave copies in flight: wait for them (bounded) before exit
-    if (tid == 0 && *vfailed)
-        for (int q = s_consumed; q < s_issued; ++q)
-            mbar_wait_bounded(&full[q % TMA_SLOTS], (unsigned)((q / TMA_SLOTS) & 1), 1024);
+    // after a failed wait: wait (standard limit) for every copy that may still be in flight
+    if (tid == 0 && *vfailed) {
+        int lo = s_done[0];
+        for (int q = 1; q < NW; ++q) lo = s_done[q] < lo ? s_done[q] : lo;
+        for (int q = lo; q < s_issued; ++q)
+            mbar_wait_bounded(&full[q % TMA_SLOTS], (unsigned)((q / TMA_SLOTS) & 1), TMA_WAIT_LIMIT);
+    }
+    __syncthreads();
     // every issued copy was waited for by the consumers (or the producer stopped
     // issuing after a failed wait); the ring is idle here
     const double wsum = warp < NW ? dfwarp_sum(wn) : 0.0;
@@ -825,7 +850,8 @@ int dst_k_project_tma(int64_t n, int nvec, const float2 *V, const float2 *w, dou
         DST_CUDA_TRY(cudaFuncSetAttribute(project_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM));
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
-    project_tma_kernel<<<nblk, TMA_THREADS, TMA_SMEM, s>>>(n, nvec, V, w, partials, gate, h, wnrm2, ticket, err);
+    project_tma_kernel<<<nblk, TMA_THREADS, TMA_SMEM, s>>>(n, nvec, V, w, partials, gate, h, wnrm2, ticket, err,
+                                                           dst_internal_wait_limit(TMA_WAIT_LIMIT));
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }

@@ -84,6 +84,10 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w) {
         cudaFree(mesh->ws);
         mesh->ws = nullptr;
         mesh->ws_bytes = 0;
+        if (dst_internal_injected_alloc_failure()) {
+            dst_internal_set_error_detail("dst_solve: workspace allocation failed (injected by dst_testing_set)");
+            return DST_ERR_OOM;
+        }
         if (cudaMalloc(&mesh->ws, total) != cudaSuccess) {
             mesh->ws = nullptr;
             cudaGetLastError();

@@ -76,6 +76,8 @@ struct dst_mesh {
     double *d_V;                  // general potential (or null)
     std::vector<double> psi0;     // host copy of the initial layer
     double2 *d_psi0;              // device copy (null until set)
+    double2 *d_bd;                // Dirichlet wall values, layers 0..N_t on the open-axis node grid
+                                  // (zero off the walls); null = homogeneous walls
     int tile_variant[2];          // apply tile shape per precision, set by the autotuner
     bool tuned;                   // the autotuner has run on this mesh
     // GMRES workspace (allocated lazily by dst_solve)
@@ -83,6 +85,12 @@ struct dst_mesh {
     size_t ws_bytes;
     double *host_pinned;          // page-locked host copy of the per-step records (lazily, by dst_solve)
 };
+
+// Testing hooks (dst_testing_set): the bulk-copy wait limit in force (the
+// standard one unless a test set another), and whether the next workspace
+// allocation is to fail as if the device were out of memory.
+unsigned dst_internal_wait_limit(unsigned standard);
+bool dst_internal_injected_alloc_failure();
 
 OpParams dst_internal_params(const dst_mesh *mesh);
 int dst_internal_update_weights(dst_mesh *mesh);
@@ -98,6 +106,8 @@ int dst_launch_rhs_d3(const OpParams &p, const double2 *psi0, double2 *b, cudaSt
 // Dispatch on the mesh dimension.
 int dst_internal_apply(const dst_mesh *mesh, int precision, const void *x, void *y, cudaStream_t s);
 int dst_internal_rhs(const dst_mesh *mesh, double2 *b, cudaStream_t s);
+// b += -D_w[unknowns, wall nodes] Psi_wall when the mesh carries wall values (boundary.cu)
+int dst_internal_rhs_walls(const dst_mesh *mesh, double2 *b, cudaStream_t s);
 // Time every apply tile variant of both precisions on scratch (at least
 // 32 * n_unknowns bytes of device memory, contents overwritten) and keep the
 // fastest in mesh->tile_variant; synchronises s.

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "internal.h"
@@ -24,6 +25,45 @@ void dst_internal_set_exception_detail(const char *call, const char *what) {
 }
 
 extern "C" const char *dst_last_error_detail(void) { return g_last_cuda_error; }
+
+// Testing hooks: process-wide knobs that make failure paths reachable without
+// faulting the GPU (see dst_testing_set in diracst.h).
+static std::atomic<long long> g_test_wait_limit{-1};     // -1: the standard limit
+static std::atomic<long long> g_test_fail_allocs{0};
+
+unsigned dst_internal_wait_limit(unsigned standard) {
+    const long long v = g_test_wait_limit.load();
+    return v < 0 ? standard : (unsigned)v;
+}
+
+bool dst_internal_injected_alloc_failure() {
+    long long v = g_test_fail_allocs.load();
+    while (v > 0)
+        if (g_test_fail_allocs.compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+
+extern "C" int dst_testing_set(int hook, int64_t value) {
+    switch (hook) {
+        case DST_TEST_WAIT_LIMIT:
+            if (value < -1 || value > 0xffffffffLL) {
+                dst_internal_set_error_detail("dst_testing_set: wait limit must be -1 or 0 .. 2^32-1");
+                return DST_ERR_ARG;
+            }
+            g_test_wait_limit.store((long long)value);
+            return DST_OK;
+        case DST_TEST_FAIL_ALLOC:
+            if (value < 0) {
+                dst_internal_set_error_detail("dst_testing_set: allocation failure count must be >= 0");
+                return DST_ERR_ARG;
+            }
+            g_test_fail_allocs.store((long long)value);
+            return DST_OK;
+        default:
+            dst_internal_set_error_detail("dst_testing_set: unknown hook");
+            return DST_ERR_ARG;
+    }
+}
 
 extern "C" const char *dst_status_string(int status) {
     switch (status) {
@@ -208,6 +248,7 @@ extern "C" int dst_create_mesh(int d, const int64_t n_el[4], const double lo[4],
     m->d_wx = nullptr;
     m->d_V = nullptr;
     m->d_psi0 = nullptr;
+    m->d_bd = nullptr;
     m->ws = nullptr;
     m->host_pinned = nullptr;
     m->tile_variant[0] = m->tile_variant[1] = 0;
@@ -234,6 +275,7 @@ extern "C" int dst_destroy_mesh(dst_mesh *mesh) {
     cudaFree(mesh->d_wx);
     cudaFree(mesh->d_V);
     cudaFree(mesh->d_psi0);
+    cudaFree(mesh->d_bd);
     cudaFree(mesh->ws);
     if (mesh->host_pinned) cudaFreeHost(mesh->host_pinned);
     cudaSetDevice(dev_prev);
@@ -332,11 +374,13 @@ int dst_internal_apply(const dst_mesh *mesh, int precision, const void *x, void 
 
 int dst_internal_rhs(const dst_mesh *mesh, double2 *b, cudaStream_t s) {
     OpParams p = dst_internal_params(mesh);
+    int rc;
     switch (mesh->d) {
-        case 1: return dst_launch_rhs_d1(p, mesh->d_psi0, b, s);
-        case 2: return dst_launch_rhs_d2(p, mesh->d_psi0, b, s);
-        default: return dst_launch_rhs_d3(p, mesh->d_psi0, b, s);
+        case 1: rc = dst_launch_rhs_d1(p, mesh->d_psi0, b, s); break;
+        case 2: rc = dst_launch_rhs_d2(p, mesh->d_psi0, b, s); break;
+        default: rc = dst_launch_rhs_d3(p, mesh->d_psi0, b, s); break;
     }
+    return rc != DST_OK ? rc : dst_internal_rhs_walls(mesh, b, s);
 }
 
 extern "C" int dst_apply_operator(const dst_mesh *mesh, int precision, const void *x, void *y, void *stream) {

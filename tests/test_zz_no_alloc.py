@@ -48,6 +48,31 @@ def test_noalloc_projection_matches_allocating_projection():
         assert np.all(np.abs(a - b) <= 1e-12 * scale), "call %d" % call
 
 
+def test_noalloc_projection_at_the_reduction_block_cap():
+    """n >= 2048 x 608 with 64 vectors: the reduction grid reaches its cap of 608
+    blocks, so the static scratch holds its largest count of partials (608 x 64);
+    a smaller call follows and must not see the first call's leftovers."""
+    import torch
+    from paper_2103_14588_gb300 import binding as B
+    lib = B.library()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    for call, (n, nvec) in enumerate([(1245184 + 977, 64), (2048 * 3 + 1, 64)]):
+        V = torch.randn(nvec * n, dtype=torch.complex128, device="cuda", generator=gen)
+        w = torch.randn(n, dtype=torch.complex128, device="cuda", generator=gen)
+        h_ref = torch.zeros(nvec, dtype=torch.complex128, device="cuda")
+        h_new = torch.full((nvec,), complex("nan+nanj"), dtype=torch.complex128, device="cuda")
+        assert lib.dst_arnoldi_project(n, nvec, _ptr(V), _ptr(w), _ptr(h_ref), stream) == B.DST_OK
+        assert lib.dst_arnoldi_project_noalloc(n, nvec, _ptr(V), _ptr(w), _ptr(h_new), stream) == B.DST_OK
+        torch.cuda.synchronize()
+        scale = (torch.linalg.vector_norm(V.view(nvec, n), dim=1) * torch.linalg.vector_norm(w)).cpu().numpy()
+        a = h_new.cpu().numpy()
+        b = h_ref.cpu().numpy()
+        assert np.all(np.isfinite(a)), "call %d" % call
+        assert np.all(np.abs(a - b) <= 1e-12 * scale), "call %d" % call
+        del V, w
+
+
 def test_noalloc_projection_rejects_too_many_vectors():
     import torch
     from paper_2103_14588_gb300 import binding as B
@@ -56,3 +81,6 @@ def test_noalloc_projection_rejects_too_many_vectors():
     rc = lib.dst_arnoldi_project_noalloc(8, 65, _ptr(x), _ptr(x), _ptr(x), None)
     assert rc == B.DST_ERR_ARG
     assert b"64" in lib.dst_last_error_detail()
+    rc = lib.dst_arnoldi_project_noalloc(0, 4, _ptr(x), _ptr(x), _ptr(x), None)
+    assert rc == B.DST_ERR_ARG
+    assert b"at least 1" in lib.dst_last_error_detail()
