@@ -1,25 +1,30 @@
 #!/usr/bin/env python
 """Benchmark: time-to-solution of the spacetime FEM Dirac solve on GB300.
 
-One step = one whole solve of the 2+1 Zitterbewegung workload (96 x 96 space
-x 96 time Q1 elements, 2-component spinor, 1,769,472 complex unknowns) to
-relative residual 1e-8: right-hand side, FP32 operator applies inside GMRES(30),
-one classical Gram-Schmidt pass per step (PETSc's GMRES default) on an
-FP32-stored Krylov basis in compensated arithmetic, FP64 Givens/least squares,
-FP64 residuals and iterative refinement.
-Inputs are resident in HBM when the timed region starts; the GMRES basis
-(31 x 28 MB) exceeds L2, so no L2 flush is needed between steps.
+One step = one whole solve of the 3+1 Klein-step workload (48^3 space x 48 time
+Q1 elements on [-6,6]^3 x [0,3], 4-component spinor, step potential V0 = 2.5 at
+x >= 0, incident packet with momentum p0 ~ U[1,3] from the seed, 20,791,296
+complex unknowns) to relative residual 1e-8: right-hand side, FP32 operator
+applies inside GMRES(30), one classical Gram-Schmidt pass per step (PETSc's
+GMRES default) on an FP32-stored Krylov basis in compensated arithmetic, FP64
+Givens/least squares, FP64 residuals and iterative refinement.  Inputs are
+resident in HBM when the timed region starts; one FP32 vector is 166 MB and the
+basis 5.2 GB, beyond the 129 MB L2, so no flush is needed between steps.
 
-Also reported on the same line: the plain-FP64-GMRES time-to-solution of the
-same system, the standalone operator-apply bandwidth (rotating buffers > 2x L2),
-the roofline of the dominant kernel class measured with CUDA events around
-every kernel of the last timed solve, the end-to-end time through the C ABI with host buffers, the
-FP64 CPU oracle timed on the host cores, and the throughput of the batched
+Also reported on the same line: the solution's error against the FP64 oracle
+at stored sample nodes; the plain-FP64-GMRES time-to-solution of the same
+system and the mixed solve with native FP64 Arnoldi; the same figures for the
+2+1 Zitterbewegung workload (96^2 x 96); the standalone operator-apply
+bandwidth and FP64 arithmetic rate of both meshes; the roofline of the
+dominant kernel class measured with CUDA events around every kernel of the
+last timed solve; the end-to-end time through the C ABI with host buffers; the
+FP64 CPU oracle timed on the host cores; and the throughput of the batched
 solve (dst_solve_batch) on two seeded sets of independent 1+1 / 2+1 solves.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-       python bench.py --ncu-case solve60|solve60_klein32|apply32_zb|apply32_klein|apply64_klein  (ncu cases)
-N > 1 runs under torch.distributed.run: independent replicas, one per GPU.
+       python bench.py --ncu-case NAME     (small fixed launches for ncu captures)
+N > 1 runs under torch.distributed.run: independent replicas, one per GPU
+(rank r solves the Klein workload of seed 1 + r).
 """
 
 import argparse
@@ -41,19 +46,18 @@ RTOL = 1e-8
 RESTART = 30
 INNER_RTOL = 1e-4
 # Gram-Schmidt of the timed solves: one classical pass per Arnoldi step, no
-# reorthogonalisation (PETSc's GMRES default); on this workload it takes the same
+# reorthogonalisation (PETSc's GMRES default); on these workloads it takes the same
 # steps to the same residual as the library's default DGKS-selective second pass
 ORTHO = 2
 HBM_FALLBACK_GBS = 6800.0
 SMS = 152
 SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_SM = 4.0     # 2 FP64 FMA per clock per SM (1/64 of the FP32 rate)
-FP32_FLOP_PER_CLK_SM = 256.0   # 128 FP32 FMA per clock per SM
-CLASSES = ("apply64", "apply32", "cast", "project", "update", "scale", "misc", "rhs")
-# DRAM read+write bytes per algorithmic byte of the projection / update on the FP32-stored
-# basis, from one ncu capture of each (profiles/gram_schmidt_f32_zb_2p1.md); valid for
-# project_f32_kernel / update_f32_kernel as committed with that file (None: not captured).
-TRAFFIC_RATIO = {"project": 1.040, "update": 0.992}
+FP64_PROBE_TFLOPS = 1.196      # FP64 FMA throughput measured by a probe kernel on this machine
+CLASSES = ("apply64", "apply32", "cast", "project", "update", "scale", "misc", "rhs", "precond")
+# DRAM read+write bytes per algorithmic byte of a kernel class, from one ncu capture of
+# its kernel as committed (profiles/*.md); None: no capture of the current kernel.
+TRAFFIC_RATIO = {}
 
 
 def measured_peaks():
@@ -64,38 +68,64 @@ def measured_peaks():
     return HBM_FALLBACK_GBS, "fallback"
 
 
-def iteration_count(name):
-    p = os.path.join(ROOT, "tests", "golden", "oracle_iteration_counts.json")
-    if os.path.exists(p):
-        d = json.load(open(p))
-        if name in d and d[name].get("converged"):
-            return d[name]["iters"]
-    return None
+def fp64_peak_tflops():
+    return SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def golden_sample(name):
+    """Stored oracle solution at sample nodes (written by oracle/solution_sample.py)."""
+    p = os.path.join(ROOT, "tests", "golden", "%s_solution_sample.json" % name)
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    d["values"] = np.array(d["re"]) + 1j * np.array(d["im"])
+    d["nodes"] = np.array(d["nodes"], dtype=np.int64)
+    return d
+
+
+def err_vs_oracle(psi, g):
+    """Relative L2 error of a device solution against the oracle's at the stored nodes."""
+    if g is None:
+        return None
+    import torch
+    idx = torch.from_numpy(g["nodes"]).to(psi.device)
+    got = psi.view(-1, g["ncomp"]).index_select(0, idx).cpu().numpy()
+    ref = g["values"]
+    return {"rel_l2_at_sampled_nodes": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_abs_over_rms": float(np.abs(got - ref).max() / (g["norm"] / np.sqrt(g["n_unknown_nodes"]))),
+            "sampled_nodes": int(len(g["nodes"])), "oracle": g.get("solver", "oracle GMRES(30) to rtol %g" % g.get("rtol", 0))}
 
 
 # ---------------------------------------------------------------- CPU oracle
 
-def oracle_seconds_per_step(w, k=4):
-    """Seconds per Arnoldi step of the oracle's GMRES(30), as it stands, on the full mesh.
+def oracle_seconds_per_step(w, restart=RESTART):
+    """Seconds of one Arnoldi step of the oracle's GMRES(restart), as it stands, on the full mesh.
 
-    Difference of two oracle solves capped at 1 and 1 + k steps (both include
-    the same initial and final residual applies), divided by k.
+    Measured parts: one oracle operator apply on a random vector, and one modified
+    Gram-Schmidt term (np.vdot and an axpy) plus one norm on full vectors; a step
+    of a GMRES(m) cycle makes on average (m + 1) / 2 Gram-Schmidt terms.
     """
-    from oracle import mesh as OM, operator as OOP, solvers as OS
+    from oracle import mesh as OM, operator as OOP
     om = OM.Mesh(w.d, w.n_el, w.lo, w.hi, w.bc)
-    b = OOP.rhs(om, w.m, w.V, w.psi0)
-    A = lambda v: OOP.apply(om, w.m, w.V, v)  # noqa: E731
+    x = W.random_complex(om.n_unknowns, 3)
+    v = W.random_complex(om.n_unknowns, 4)
     t0 = time.perf_counter()
-    OS.gmres(A, b, restart=RESTART, rtol=RTOL, maxiter=1)
+    y = OOP.apply(om, w.m, w.V, x)
     t1 = time.perf_counter()
-    OS.gmres(A, b, restart=RESTART, rtol=RTOL, maxiter=1 + k)
+    h = np.vdot(v, y)
+    y = y - h * v
+    np.linalg.norm(y)
     t2 = time.perf_counter()
-    return max((t2 - t1) - (t1 - t0), 1e-9) / k
+    return (t1 - t0) + 0.5 * (restart + 1) * (t2 - t1), t1 - t0, t2 - t1
 
 
 def replica_seed(rank):
-    """Seed of the bench workload on a rank: independent replicas draw independent packets."""
-    return 20210326 + rank
+    """Seed of the bench workload on a rank: independent replicas draw independent momenta."""
+    return 1 + rank
+
+
+def headline_workload(rank=0):
+    return W.klein_3p1(seed=replica_seed(rank))
 
 
 def aggregate_timing(t_ms, world, steps, dist=None, device="cuda"):
@@ -127,26 +157,36 @@ def host_cores():
     return os.cpu_count() or 1
 
 
+def oracle_step_count():
+    g = golden_sample("klein_3p1_seed1")
+    return None if g is None else g["gmres30_iters_rtol_1e-8"]
+
+
+def cpu_sample_text(sec_step, t_apply, t_gs, n_iter):
+    return ("oracle (FP64 numpy) on the full 48^3 x 48 Klein system: one operator apply (%.2f s) + "
+            "(m+1)/2 = %.1f modified Gram-Schmidt terms (vdot + axpy + norm, %.3f s each) = %.2f s per "
+            "GMRES(%d) step, times the oracle's own %d-step count to 1e-8 (stacked 1+1 reduction, "
+            "tests/golden/klein_3p1_seed1_solution_sample.json)"
+            % (t_apply, 0.5 * (RESTART + 1), t_gs, sec_step, RESTART, n_iter))
+
+
 def run_reference(args, rank):
     """The FP64 CPU oracle on the host cores, same workload / metric / unit."""
     if rank != 0:
         return
-    w = W.zb_2p1()
-    n_iter = iteration_count("zb_2p1")
-    k = 2
-    for _ in range(args.warmup):
-        oracle_seconds_per_step(w, k)
-    per = [oracle_seconds_per_step(w, k) for _ in range(args.steps)]
-    sec_step = statistics.mean(per)
+    w = headline_workload(0)
+    n_iter = oracle_step_count()
     if n_iter is None:
-        print(json.dumps({"impl": "reference", "unavailable": "oracle GMRES step count for zb_2p1 not recorded "
-                          "(run python -m oracle.iteration_counts)"}))
+        print(json.dumps({"impl": "reference", "unavailable": "oracle GMRES step count for klein_3p1 seed 1 not "
+                          "recorded (run python -m oracle.solution_sample klein_3p1_seed1)"}))
         return
+    for _ in range(args.warmup):
+        oracle_seconds_per_step(w)
+    per = [oracle_seconds_per_step(w) for _ in range(args.steps)]
+    sec_step = statistics.mean(p[0] for p in per)
     solve_s = sec_step * n_iter
     value = 1.0 / solve_s
-    sample = ("each step: the oracle's GMRES(%d) from x0 = 0 on the full 96x96x96 system for 1 and %d Arnoldi "
-              "steps; the difference / %d is the seconds per step, times the oracle's own %d-step solve "
-              "(rel. resid %g) recorded by oracle/iteration_counts.py" % (RESTART, 1 + k, k, n_iter, RTOL))
+    sample = cpu_sample_text(sec_step, statistics.mean(p[1] for p in per), statistics.mean(p[2] for p in per), n_iter)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * solve_s,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -160,12 +200,14 @@ def run_reference(args, rank):
 # ---------------------------------------------------------------- GPU arm
 
 METRIC = "operator-apply HBM GB/s; time-to-solution at rel. resid 1e-8 vs plain FP64 GMRES"
-CONFIG = {"workload": "zb_2p1: 2+1 Zitterbewegung packet (sigma 0.5, p0 (2,0), seed 20210326), Q1 mesh "
-                      "96x96 space x 96 time on [-8,8]^2 x [0,4], periodic, m = 1, NC = 2, 1769472 complex "
+CONFIG = {"workload": "klein_3p1: 3+1 Klein step (V0 = 2.5 m at x >= 0), Q1 tesseract mesh 48^3 space x 48 time "
+                      "on [-6,6]^3 x [0,3], x Dirichlet walls, y, z periodic, m = 1, NC = 4, incident packet "
+                      "(sigma 0.5 at x = -2) with p0 ~ U[1,3] from seed 1 (p0 = 2.133), 20791296 complex "
                       "unknowns; GMRES(30) with FP32 operator apply inside FP64 iterative refinement to "
                       "rel. resid 1e-8",
-          "unknowns": 1769472, "rtol": RTOL, "restart": RESTART, "inner_rtol": INNER_RTOL,
-          "l2": "working set > L2 (FP32 GMRES basis 31 x 14 MB = 439 MB), no flush", "parallelism": "replicas",
+          "unknowns": 20791296, "rtol": RTOL, "restart": RESTART, "inner_rtol": INNER_RTOL,
+          "l2": "working set > L2 (FP32 vector 166 MB, FP32 GMRES basis 31 x 166 MB = 5.2 GB), no flush",
+          "parallelism": "replicas (rank r: seed 1 + r)",
           "gram_schmidt": "one classical pass per step (ortho = 2), mixed and FP64 solves alike"}
 
 
@@ -337,6 +379,42 @@ def run_batch_bench(torch, B):
     return out
 
 
+def timed_solve(torch, B, mesh, opts, psi):
+    """One solve bracketed by CUDA events on the current stream; (seconds, stats)."""
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    st = B.dst_solve(mesh, opts, psi)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) * 1e-3, st
+
+
+def apply_figures(torch, B, mesh_obj, st_prof, hbm):
+    """Standalone FP32 / FP64 apply: time, HBM GB/s and the FP64 arithmetic rate
+    (algorithmic flops per apply from the solver's accounting)."""
+    n = mesh_obj.n_unknowns
+    a32_ms, a32_gbs = time_apply(torch, B, mesh_obj.handle, B.DST_FP32, n)
+    a64_ms, a64_gbs = time_apply(torch, B, mesh_obj.handle, B.DST_FP64, n)
+    i64, i32 = CLASSES.index("apply64"), CLASSES.index("apply32")
+    fl = None
+    for i in (i64, i32):
+        if st_prof["kernel_launches"][i] > 0:
+            fl = st_prof["kernel_flops"][i] / st_prof["kernel_launches"][i]
+            break
+    out = {"fp32_gbs": a32_gbs, "fp32_us": 1e3 * a32_ms, "fp32_frac_of_hbm": a32_gbs / hbm,
+           "fp64_gbs": a64_gbs, "fp64_us": 1e3 * a64_ms, "fp64_frac_of_hbm": a64_gbs / hbm,
+           "bytes_per_unknown": {"fp32": 16, "fp64": 32}}
+    if fl:
+        tf64 = fl / (a64_ms * 1e-3) / 1e12
+        out.update({"flops_per_apply": fl, "fp64_tflops": tf64, "fp64_frac_of_fp64_peak": tf64 / fp64_peak_tflops(),
+                    "fp64_frac_of_probe": tf64 / FP64_PROBE_TFLOPS,
+                    "fp64_peak_kind": "152 SMs x 4 FLOP/clk x 2070 MHz = %.3f TFLOP/s (derived); a probe kernel "
+                                      "measured %.3f" % (fp64_peak_tflops(), FP64_PROBE_TFLOPS),
+                    "fp32_tflops": fl / (a32_ms * 1e-3) / 1e12})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,6 +423,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve throughput cases")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed solves (no FP64 comparisons, second workload, applies)")
     ap.add_argument("--ncu-case", choices=NCU_CASES, help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.ncu_case:
@@ -370,7 +450,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    w = W.zb_2p1(seed=replica_seed(rank))
+    w = headline_workload(rank)
     mesh_obj = B.Mesh.from_workload(w)
     mesh = mesh_obj.handle
     n = mesh_obj.n_unknowns
@@ -378,7 +458,7 @@ def main():
     # one classical Gram-Schmidt pass per step (PETSc's GMRES default, ORTHO) in every timed
     # solve, mixed and plain FP64 alike
     opts = {"restart": RESTART, "rtol": RTOL, "max_iters": 200000, "mixed_precision": 1,
-            "inner_rtol": INNER_RTOL, "max_refine": 60, "ortho": ORTHO}
+            "inner_rtol": INNER_RTOL, "max_refine": 100000, "ortho": ORTHO}
 
     for _ in range(args.warmup):
         B.dst_solve(mesh, opts, psi)
@@ -403,19 +483,17 @@ def main():
         torch.cuda.synchronize()
         barrier()
     t_ms, value = aggregate_timing(e0.elapsed_time(e1), world, args.steps, dist)
-    for s in stats:
-        if s["status"] != 0:
-            raise RuntimeError("timed solve did not converge: %s" % s)
+    for st_ in stats:
+        if st_["status"] != 0:
+            raise RuntimeError("timed solve did not converge: %s" % st_)
 
     # per-class kernel accounting over the profiled (last) timed solve; launches over all
     tot = {k: [0.0, 0.0, 0.0, 0.0] for k in CLASSES}
-    launches = sum(int(s["launches"]) for s in stats)
-    for s in stats[-1:]:
-        for i, k in enumerate(CLASSES):
-            tot[k][0] += s["kernel_ms"][i]
-            tot[k][1] += s["kernel_launches"][i]
-            tot[k][2] += s["kernel_bytes"][i]
-            tot[k][3] += s["kernel_flops"][i]
+    launches = sum(int(st_["launches"]) for st_ in stats)
+    st_prof = stats[-1]
+    for i, k in enumerate(CLASSES):
+        tot[k] = [st_prof["kernel_ms"][i], st_prof["kernel_launches"][i], st_prof["kernel_bytes"][i],
+                  st_prof["kernel_flops"][i]]
     kms = sum(v[0] for v in tot.values())
 
     if rank != 0:
@@ -424,53 +502,71 @@ def main():
 
     hbm, hbm_kind = measured_peaks()
     clocks = clk.summary()
-    mhz = clocks["sm_mhz"] or SM_MAX_MHZ
-    fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s at max clock
+    err_headline = err_vs_oracle(psi, golden_sample("klein_3p1_seed1"))
     dom = max(CLASSES, key=lambda k: tot[k][0])
     d_ms, d_l, d_b, d_f = tot[dom]
-    # in the timed mixed solve only the FP64 operator apply is bound by the FP64
-    # pipe; every other class streams HBM
-    fp64_classes = ("apply64",)
-    if dom in fp64_classes and d_f > 0:
+    if dom == "apply64" and d_f > 0:
         ach = d_f / (d_ms * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None,
-                "peak_kind": "FP64 FMA pipe: 152 SMs x 4 FLOP/clk x 2070 MHz (derived; probe measured 1.196)",
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp64_peak_tflops(), "unit": "TFLOP/s",
+                "frac": ach / fp64_peak_tflops(), "traffic": None,
+                "peak_kind": "FP64 FMA pipe: 152 SMs x 4 FLOP/clk x 2070 MHz (derived; probe measured %.3f)"
+                             % FP64_PROBE_TFLOPS,
                 "achieved_gbs": d_b / (d_ms * 1e-3) / 1e9, "hbm_frac": d_b / (d_ms * 1e-3) / 1e9 / hbm,
                 "avg_launch_us": 1e3 * d_ms / max(d_l, 1)}
     else:
         ach = d_b / (d_ms * 1e-3) / 1e9
-        traffic = None
         launches_ran = d_l
         if dom in ("project", "update"):
-            # per step one first-pass launch plus one gated second pass, which moves data
-            # only when it runs (reorths); achieved = bytes per launch / time per launch
-            launches_ran = sum(s["iters"] + s["reorths"] for s in stats[-1:])
-        if TRAFFIC_RATIO.get(dom):
-            # average algorithmic bytes per launch that ran times the measured DRAM/algorithmic ratio
-            traffic = TRAFFIC_RATIO[dom] * d_b / max(launches_ran, 1)
+            # per step one first-pass launch (a gated second pass moves data only when it runs)
+            launches_ran = st_prof["iters"] + st_prof["reorths"] + (st_prof["restarts"] if dom == "update" else 0)
+        traffic = TRAFFIC_RATIO[dom] * d_b / max(launches_ran, 1) if TRAFFIC_RATIO.get(dom) else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": traffic, "traffic_unit": "bytes per launch", "peak_kind": hbm_kind,
                 "algorithmic_bytes_per_launch": d_b / max(launches_ran, 1),
                 "avg_launch_us": 1e3 * d_ms / max(launches_ran, 1)}
     kernels = {k: {"ms_share": (v[0] / kms if kms else None), "launches": int(v[1]),
                    "GBps": (v[2] / (v[0] * 1e-3) / 1e9 if v[0] else None),
-                   "TFLOPps": (v[3] / (v[0] * 1e-3) / 1e12 if v[0] else None)} for k, v in tot.items() if v[1]}
+                   "TFLOPps": (v[3] / (v[0] * 1e-3) / 1e12 if v[0] and v[3] else None)} for k, v in tot.items() if v[1]}
 
-    # plain FP64 GMRES(30) on the same system (comparison, outside the timed region)
-    fp64_opts = {"restart": RESTART, "rtol": RTOL, "max_iters": 200000, "mixed_precision": 0, "ortho": ORTHO}
-    B.dst_solve(mesh, fp64_opts, psi)
-    torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record()
-    st64 = B.dst_solve(mesh, fp64_opts, psi)
-    f1.record()
-    torch.cuda.synchronize()
-    fp64_s = f0.elapsed_time(f1) * 1e-3
-
-    # standalone operator apply bandwidth (FP32 and FP64)
-    a32_ms, a32_gbs = time_apply(torch, B, mesh, B.DST_FP32, n)
-    a64_ms, a64_gbs = time_apply(torch, B, mesh, B.DST_FP64, n)
+    extras = {}
+    if not args.no_extras:
+        # native FP64 Arnoldi (mixed_ortho = 1, library-default DGKS second pass) inside the same
+        # mixed refinement, and plain FP64 GMRES(30) on the same system
+        psi2 = torch.zeros_like(psi)
+        t_fa, st_fa = timed_solve(torch, B, mesh, dict(opts, mixed_ortho=1, ortho=0), psi2)
+        t64, st64 = timed_solve(torch, B, mesh, {"restart": RESTART, "rtol": RTOL, "max_iters": 200000,
+                                                 "mixed_precision": 0, "ortho": ORTHO}, psi2)
+        extras["fp64_arnoldi_mixed"] = {"time_to_solution_s": t_fa, "iters": st_fa["iters"],
+                                        "reorths": st_fa["reorths"], "rel_resid_true": st_fa["rel_resid_true"],
+                                        "vs_headline": t_fa / (t_ms * 1e-3 / args.steps),
+                                        "what": "mixed refinement with the Krylov basis and Gram-Schmidt in native "
+                                                "FP64 (DGKS-selective second pass)"}
+        extras["fp64_gmres"] = {"time_to_solution_s": t64, "iters": st64["iters"], "restarts": st64["restarts"],
+                                "reorths": st64["reorths"], "rel_resid_true": st64["rel_resid_true"],
+                                "err_vs_oracle": err_vs_oracle(psi2, golden_sample("klein_3p1_seed1")),
+                                "mixed_speedup": t64 / (t_ms * 1e-3 / args.steps)}
+        del psi2
+        extras["apply"] = dict(apply_figures(torch, B, mesh_obj, st_prof, hbm), hbm_peak=hbm, peak_kind=hbm_kind)
+        # the 2+1 Zitterbewegung workload (96^2 x 96, 1,769,472 unknowns)
+        wz = W.zb_2p1()
+        with B.Mesh.from_workload(wz) as mz:
+            pz = torch.zeros(mz.n_unknowns, dtype=torch.complex128, device="cuda")
+            B.dst_solve(mz.handle, opts, pz)
+            zt = [timed_solve(torch, B, mz.handle, opts, pz) for _ in range(3)]
+            tz = statistics.median(t for t, _ in zt)
+            stz = zt[-1][1]
+            ezb = err_vs_oracle(pz, golden_sample("zb_2p1"))
+            _, stzp = timed_solve(torch, B, mz.handle, dict(opts, profile=1), pz)
+            pz2 = torch.zeros_like(pz)
+            tz64, stz64 = timed_solve(torch, B, mz.handle, {"restart": RESTART, "rtol": RTOL, "max_iters": 200000,
+                                                            "mixed_precision": 0, "ortho": ORTHO}, pz2)
+            extras["zb_2p1"] = {"unknowns": mz.n_unknowns, "time_to_solution_s": tz, "solves_per_s": 1.0 / tz,
+                                "iters": stz["iters"], "rel_resid_true": stz["rel_resid_true"], "err_vs_oracle": ezb,
+                                "fp64_gmres": {"time_to_solution_s": tz64, "iters": stz64["iters"],
+                                               "rel_resid_true": stz64["rel_resid_true"],
+                                               "err_vs_oracle": err_vs_oracle(pz2, golden_sample("zb_2p1"))},
+                                "mixed_speedup": tz64 / tz,
+                                "apply": apply_figures(torch, B, mz, stzp, hbm)}
 
     # end to end through the C ABI with host buffers: psi0 from pinned host memory in,
     # solution to pinned host memory out, every step
@@ -494,31 +590,26 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline:
-        sec_step = oracle_seconds_per_step(w, k=2)
-        n_or = iteration_count("zb_2p1")
-        src = "the oracle's own %s-step solve recorded by oracle/iteration_counts.py" % n_or
+        n_or = oracle_step_count()
+        src_iters = n_or
         if n_or is None:
-            n_or = st64["iters"]
-            src = "the %d Arnoldi steps the FP64 GPU GMRES took on this system" % n_or
+            n_or = stats[-1]["iters"]
+        sec_step, t_apply, t_gs = oracle_seconds_per_step(w)
         cpu = {"value": 1.0 / (sec_step * n_or), "unit": "solves/s", "cores": host_cores(), "kind": "oracle",
-               "sample": "oracle GMRES(30), FP64 numpy, on the full 96x96x96 system for 1 and 3 Arnoldi steps "
-                         "(difference / 2 = %.3f s per step), times %s" % (sec_step, src)}
+               "sample": cpu_sample_text(sec_step, t_apply, t_gs, n_or) +
+                         ("" if src_iters else " (count: the GPU solve's own steps)")}
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 apply and Krylov basis; df32 (compensated f32) Gram-Schmidt; f64 residual, Givens, refinement", "data": "synthetic",
-        "config": CONFIG,
+        "vs_baseline": None,
+        "dtype": "f32 apply and Krylov basis; df32 (compensated f32) Gram-Schmidt; f64 residual, Givens, refinement",
+        "data": "synthetic", "config": CONFIG,
         "time_to_solution_s": t_ms * 1e-3 / args.steps,
         "solve": {"iters": stats[-1]["iters"], "restarts": stats[-1]["restarts"],
                   "refinements": stats[-1]["refinements"], "reorths": stats[-1]["reorths"],
                   "rel_resid_true": stats[-1]["rel_resid_true"]},
-        "fp64_gmres": {"time_to_solution_s": fp64_s, "iters": st64["iters"], "restarts": st64["restarts"],
-                       "reorths": st64["reorths"],
-                       "rel_resid_true": st64["rel_resid_true"], "mixed_speedup": fp64_s / (t_ms * 1e-3 / args.steps)},
-        "apply": {"fp32_gbs": a32_gbs, "fp32_us": 1e3 * a32_ms, "fp32_frac_of_hbm": a32_gbs / hbm,
-                  "fp64_gbs": a64_gbs, "fp64_us": 1e3 * a64_ms, "fp64_frac_of_hbm": a64_gbs / hbm,
-                  "hbm_peak": hbm, "peak_kind": hbm_kind, "bytes_per_unknown": {"fp32": 16, "fp64": 32}},
+        "err_vs_oracle": err_headline,
         "roofline": roof,
         "roofline_source": "CUDA events around every kernel of the last timed solve",
         "apply_tile_variant": {"fp32": B.dst_get_apply_variant(mesh, B.DST_FP32)[0],
@@ -530,6 +621,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    line.update(extras)
     print(json.dumps(line))
     barrier()
     mesh_obj.close()

@@ -229,6 +229,14 @@ typedef struct {
     int batch_cta_max;      /* dst_solve_batch only: meshes of at most this many unknowns are
                                solved one CTA each inside a persistent kernel, larger ones by
                                concurrent single-mesh solves; negative = automatic (default) */
+    int precond;            /* right preconditioner (DST_PRECOND_*, default NONE).  With one, the
+                               inner GMRES becomes flexible GMRES (Saad 1993): each Arnoldi step
+                               applies the operator to z_j = M(v_j), the z_j are kept (FP32), and a
+                               cycle's correction is Z y.  Needs mixed_precision = 1,
+                               mixed_ortho = 2, inner_cycles = 1, method = 0.
+                               DST_PRECOND_CN_SWEEP2 applies the sweep twice per step,
+                               z = M v + M (v - A M v).  dst_solve_batch honours it for the meshes
+                               it solves one by one and ignores it in the persistent kernel */
 } dst_solve_opts;
 
 /* Kernel classes of dst_solve_stats' per-class arrays. */
@@ -241,7 +249,8 @@ enum {
     DST_K_SCALE = 5,        /* basis normalisation */
     DST_K_MISC = 6,         /* residuals, norms, x += d */
     DST_K_RHS = 7,          /* right-hand side */
-    DST_NUM_KERNEL_CLASSES = 8
+    DST_K_PRECOND = 8,      /* preconditioner (Crank-Nicolson sweep: scan, FFTs, march) */
+    DST_NUM_KERNEL_CLASSES = 9
 };
 
 typedef struct {
@@ -255,17 +264,17 @@ typedef struct {
     double bytes_moved;     /* algorithmic device bytes of the kernels launched */
     double launches;        /* kernel launches of the call */
     int reorths;            /* Arnoldi steps that took a second Gram-Schmidt pass */
-    double kernel_ms[8];        /* device time per DST_K_* class (opts.profile only, else 0) */
-    double kernel_launches[8];  /* kernel launches per class */
-    double kernel_bytes[8];     /* algorithmic bytes per class (reads + writes) */
-    double kernel_flops[8];     /* algorithmic floating-point operations per class */
+    double kernel_ms[9];        /* device time per DST_K_* class (opts.profile only, else 0) */
+    double kernel_launches[9];  /* kernel launches per class */
+    double kernel_bytes[9];     /* algorithmic bytes per class (reads + writes) */
+    double kernel_flops[9];     /* algorithmic floating-point operations per class */
 } dst_solve_stats;
 
 /* Fill opts with the defaults (restart 30, max_iters 100000, rtol 1e-8,
  * FP64, inner_rtol 1e-4, max_refine 100000, zero initial guess, no
  * profiling, one inner cycle per refinement, classical Gram-Schmidt with a
  * DGKS-selective second pass, inner Gram-Schmidt on an FP32-stored basis in
- * compensated arithmetic, GMRES). */
+ * compensated arithmetic, GMRES, no preconditioner). */
 DST_API int dst_default_solve_opts(dst_solve_opts *opts);
 
 /*
@@ -367,6 +376,29 @@ DST_API int dst_observables(const dst_mesh *mesh, const void *psi, double x0, vo
  */
 enum { DST_TEST_WAIT_LIMIT = 1, DST_TEST_FAIL_ALLOC = 2 };
 DST_API int dst_testing_set(int hook, int64_t value);
+
+/*
+ * Right preconditioners for flexible GMRES (dst_solve_opts.precond).  The paper
+ * names none; its conclusion (Sec. 5) asks for one and points at decomposing
+ * the time direction.
+ *   DST_PRECOND_CN_SWEEP  the Crank-Nicolson sweep M = B^-1 S^-1: S averages
+ *     adjacent time layers (S = (I + U) / 2, U the shift to the next layer, the
+ *     last layer keeping 1/2) and B is the block lower-bidiagonal
+ *     Crank-Nicolson march B[t,t] = i M_s + (h_t/2) K_s, B[t,t-1] = -i M_s +
+ *     (h_t/2) K_s, with M_s the spatial mass matrix and K_s the spatial part of
+ *     Eq. 7's operator (Appendix A's element matrices).  Meshes whose spatial axes
+ *     are all periodic with a constant potential (1+1, 2+1), or whose x axis is
+ *     Dirichlet, the others periodic and the potential depends on x only
+ *     (1+1, 2+1, 3+1).  Other meshes: DST_ERR_ARG.
+ * dst_precond_apply: z = M v for DEVICE FP32 complex vectors v, z of
+ * n_unknowns entries (float pairs, the unknown layout), distinct; arithmetic in
+ * FP32 (the precision of the inner solve), the layer-solve factors in FP64
+ * rounded to FP32.  Takes stream-ordered scratch of about one FP32 vector (plus
+ * the factors, 32 NC^2 bytes per x node and frequency, on Dirichlet-x meshes).
+ * Errors: DST_ERR_ARG (kind, mesh not covered), DST_ERR_OOM, DST_ERR_CUDA.
+ */
+enum { DST_PRECOND_NONE = 0, DST_PRECOND_CN_SWEEP = 1, DST_PRECOND_CN_SWEEP2 = 2 };
+DST_API int dst_precond_apply(const dst_mesh *mesh, int kind, const void *v, void *z, void *stream);
 
 /* Static, human-readable name of a status code. */
 DST_API const char *dst_status_string(int status);

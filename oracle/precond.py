@@ -23,8 +23,10 @@ each returning a callable v -> M v for ``solvers.fgmres``:
   function is a half hat, keeps 1/2 only), reproduces the time-derivative
   terms of D_w22 exactly and its spatial terms up to (h_t/12) K_s times the
   second difference in time (and h_t/12 K_s (x_N - x_{N-1}) on the last
-  layer).  The preconditioner is M = B^-1 S^-1: a backward sweep for S and a
-  forward Crank-Nicolson march for B, one spatial solve per layer.
+  layer).  The preconditioner is M = B^-1 S^-1: a backward sweep for S
+  (s_{N-1} = 2 v_{N-1}, s_t = 2 v_t - s_{t+1}) and a forward Crank-Nicolson
+  march for B (x_0 = Bd^-1 s_0, x_t = Bd^-1 (s_t - Bl x_{t-1})), one spatial
+  solve with the LU factors of Bd per layer.
 
 The unknown vector is ordered [t][z][y][x][c] (time slowest), so a time
 layer is a contiguous run of ``per`` = n_spatial_nodes * NC entries and a
@@ -40,6 +42,7 @@ the last for data linear in time, and M inverts S B.
 """
 
 import numpy as np
+import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
@@ -99,19 +102,28 @@ def crank_nicolson_sweep(A, nt, per):
     htK = (3.0 * (up + down)).tocsr()                       # 2 (h_t/6) K_s * 3 = h_t K_s
     Bd = (1j * Ms + 0.5 * htK).tocsr()
     Bl = (-1j * Ms + 0.5 * htK).tocsr()
-    B = sp.lil_matrix(A.shape, dtype=np.complex128)
-    S = sp.lil_matrix(A.shape, dtype=np.complex128)
-    eye = sp.eye(per, format="csr")
-    for t in range(nt):
-        B[t * per:(t + 1) * per, t * per:(t + 1) * per] = Bd
-        S[t * per:(t + 1) * per, t * per:(t + 1) * per] = 0.5 * eye
-        if t > 0:
-            B[t * per:(t + 1) * per, (t - 1) * per:t * per] = Bl
-        if t < nt - 1:
-            S[t * per:(t + 1) * per, (t + 1) * per:(t + 2) * per] = 0.5 * eye
-    B, S = B.tocsc(), S.tocsc()
-    Blu, Slu = spla.splu(B), spla.splu(S)
+    # block (t, t) = Bd, block (t, t - 1) = Bl; S: block (t, t) = (t, t + 1) = I / 2
+    lower = sp.eye(nt, k=-1, format="csr")
+    B = (sp.kron(sp.eye(nt, format="csr"), Bd) + sp.kron(lower, Bl)).astype(np.complex128)
+    S = (0.5 * sp.kron(sp.eye(nt, format="csr") + sp.eye(nt, k=1, format="csr"), sp.eye(per, format="csr")))
+    B, S = B.tocsc(), S.astype(np.complex128).tocsc()
+    # one factorisation of the layer matrix Bd serves every layer of the march
+    if per <= 4096:
+        lu = sla.lu_factor(Bd.toarray())
+        solve_Bd = lambda r: sla.lu_solve(lu, r)                      # noqa: E731
+    else:
+        slu = spla.splu(Bd.tocsc())
+        solve_Bd = slu.solve
 
     def apply(v):
-        return Blu.solve(Slu.solve(np.asarray(v, dtype=np.complex128)))
+        V = np.asarray(v, dtype=np.complex128).reshape(nt, per)
+        s_ = np.empty_like(V)                         # S^-1: backward over the layers
+        s_[-1] = 2.0 * V[-1]
+        for t in range(nt - 2, -1, -1):
+            s_[t] = 2.0 * V[t] - s_[t + 1]
+        x = np.empty_like(V)                          # B^-1: the forward Crank-Nicolson march
+        x[0] = solve_Bd(s_[0])
+        for t in range(1, nt):
+            x[t] = solve_Bd(s_[t] - Bl @ x[t - 1])
+        return x.ravel()
     return apply, S, B, Ms, htK

@@ -21,6 +21,7 @@ DST_ERR_ARG, DST_ERR_OOM, DST_ERR_CUDA, DST_ERR_NAN, DST_ERR_STATE = -1, -2, -3,
 DST_BC_PERIODIC, DST_BC_OPEN, DST_BC_DIRICHLET = 0, 1, 2
 DST_FP64, DST_FP32 = 0, 1
 DST_TEST_WAIT_LIMIT, DST_TEST_FAIL_ALLOC = 1, 2
+DST_PRECOND_NONE, DST_PRECOND_CN_SWEEP, DST_PRECOND_CN_SWEEP2 = 0, 1, 2
 
 EXPORTED = (
     "dst_create_mesh", "dst_destroy_mesh", "dst_mesh_sizes", "dst_set_mass", "dst_set_potential",
@@ -28,7 +29,7 @@ EXPORTED = (
     "dst_arnoldi_update", "dst_default_solve_opts", "dst_solve", "dst_status_string",
     "dst_last_error_detail", "dst_arnoldi_project_noalloc", "dst_observables", "dst_solve_batch",
     "dst_tune_apply", "dst_set_apply_variant", "dst_get_apply_variant", "dst_testing_set",
-    "dst_set_boundary_data",
+    "dst_set_boundary_data", "dst_precond_apply",
 )
 
 
@@ -46,7 +47,8 @@ class dst_solve_opts(ctypes.Structure):
                 ("mixed_precision", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("use_initial_guess", ctypes.c_int),
                 ("profile", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("ortho", ctypes.c_int),
-                ("mixed_ortho", ctypes.c_int), ("method", ctypes.c_int), ("batch_cta_max", ctypes.c_int)]
+                ("mixed_ortho", ctypes.c_int), ("method", ctypes.c_int), ("batch_cta_max", ctypes.c_int),
+                ("precond", ctypes.c_int)]
 
 
 class dst_solve_stats(ctypes.Structure):
@@ -54,8 +56,8 @@ class dst_solve_stats(ctypes.Structure):
                 ("status", ctypes.c_int), ("rel_resid_true", ctypes.c_double),
                 ("rel_resid_est", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("bytes_moved", ctypes.c_double), ("launches", ctypes.c_double), ("reorths", ctypes.c_int),
-                ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_double * 8),
-                ("kernel_bytes", ctypes.c_double * 8), ("kernel_flops", ctypes.c_double * 8)]
+                ("kernel_ms", ctypes.c_double * 9), ("kernel_launches", ctypes.c_double * 9),
+                ("kernel_bytes", ctypes.c_double * 9), ("kernel_flops", ctypes.c_double * 9)]
 
     def as_dict(self):
         out = {}
@@ -65,7 +67,7 @@ class dst_solve_stats(ctypes.Structure):
         return out
 
 
-KERNEL_CLASSES = ("apply64", "apply32", "cast", "project", "update", "scale", "misc", "rhs")
+KERNEL_CLASSES = ("apply64", "apply32", "cast", "project", "update", "scale", "misc", "rhs", "precond")
 
 
 def _load():
@@ -98,6 +100,7 @@ def _load():
         "dst_status_string": (ctypes.c_char_p, [c_int]),
         "dst_last_error_detail": (ctypes.c_char_p, []),
         "dst_testing_set": (c_int, [c_int, i64]),
+        "dst_precond_apply": (c_int, [vp, c_int, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -261,6 +264,15 @@ def dst_arnoldi_update(n, nvec, V, h, w, nrm2, stream=None):
     pn = _dev_ptr(nrm2, torch.float64, 1, "nrm2")
     return _check(_lib.dst_arnoldi_update(int(n), int(nvec), pV, ph, pw, pn, _stream(stream, V, w)),
                   "dst_arnoldi_update")
+
+
+def dst_precond_apply(mesh, kind, v, z, stream=None):
+    """z = M v for the preconditioner `kind` (complex64 CUDA tensors of n_unknowns entries)."""
+    import torch
+    _, nu, _ = dst_mesh_sizes(mesh)
+    pv = _dev_ptr(v, torch.complex64, nu, "v")
+    pz = _dev_ptr(z, torch.complex64, nu, "z")
+    return _check(_lib.dst_precond_apply(mesh, int(kind), pv, pz, _stream(stream, v, z)), "dst_precond_apply")
 
 
 def dst_observables(mesh, psi, x0, out, stream=None):

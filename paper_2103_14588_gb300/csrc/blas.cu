@@ -406,6 +406,36 @@ int dst_k_bicg_s(int64_t n, const double2 *r, const double2 *v, double2 *sv, con
     return DST_OK;
 }
 
+namespace {
+// r = v - a (FP32 complex vectors)
+__global__ void sub_f32_kernel(int64_t n, const float2 *__restrict__ v, const float2 *__restrict__ a,
+                               float2 *__restrict__ r) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 x = v[i], y = a[i];
+        r[i] = make_float2(x.x - y.x, x.y - y.y);
+    }
+}
+// z += a
+__global__ void add_f32_kernel(int64_t n, const float2 *__restrict__ a, float2 *__restrict__ z) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 x = z[i], y = a[i];
+        z[i] = make_float2(x.x + y.x, x.y + y.y);
+    }
+}
+}  // namespace
+
+int dst_k_sub_f32(int64_t n, const float2 *v, const float2 *a, float2 *r, cudaStream_t s) {
+    sub_f32_kernel<<<stream_blocks(n), 256, 0, s>>>(n, v, a, r);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
+int dst_k_add_f32(int64_t n, const float2 *a, float2 *z, cudaStream_t s) {
+    add_f32_kernel<<<stream_blocks(n), 256, 0, s>>>(n, a, z);
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
 int dst_k_axpy1(int64_t n, const double2 *d, double2 *x, cudaStream_t s) {
     axpy1_kernel<<<stream_blocks(n), 256, 0, s>>>(n, d, x);
     DST_CUDA_TRY(cudaGetLastError());

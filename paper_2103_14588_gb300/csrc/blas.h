@@ -21,6 +21,8 @@ int dst_k_scale(int64_t n, const double2 *src, double2 *dst, const double *nrm2,
 int dst_k_cast_64_32(int64_t n, const double2 *src, float2 *dst, cudaStream_t s);
 int dst_k_cast_32_64(int64_t n, const float2 *src, double2 *dst, cudaStream_t s);
 int dst_k_axpy1(int64_t n, const double2 *d, double2 *x, cudaStream_t s);
+int dst_k_sub_f32(int64_t n, const float2 *v, const float2 *a, float2 *r, cudaStream_t s);   // r = v - a
+int dst_k_add_f32(int64_t n, const float2 *a, float2 *z, cudaStream_t s);                     // z += a
 int dst_k_reduce_partials(int nblk, int nvec, const double2 *partials, double2 *out, cudaStream_t s,
                           const double *gate = nullptr);
 int dst_k_reduce_real(int nblk, const double *partials, double *out, cudaStream_t s, const double *gate = nullptr,

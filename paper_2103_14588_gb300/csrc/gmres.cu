@@ -27,6 +27,7 @@
 
 #include "blas.h"
 #include "internal.h"
+#include "sweep.h"
 
 namespace {
 
@@ -46,6 +47,10 @@ struct Workspace {
     double *host;      // pinned, 2 * 2 * (m + 1) + 8 doubles
     double *host_cols; // pinned, DST_MAX_VEC * COL_STRIDE doubles
     void *dev_base;
+    // flexible GMRES (preconditioned mixed solve): the preconditioned directions
+    // z_j (m FP32 vectors), two FP32 vectors for the second sweep, the sweep's scratch
+    float2 *Z, *pr, *pz2;
+    void *sweep_scratch;
 };
 
 // One Arnoldi step's record in Workspace::cols: first-pass coefficients
@@ -60,7 +65,7 @@ constexpr int64_t TMA_MIN_UNKNOWNS = 4000000;
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w) {
+int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w, int precond = 0, size_t sweep_bytes = 0) {
     const int64_t n = mesh->n_unknowns;
     const int nblk = DST_MAX_RED_BLOCKS;
     size_t off = 0;
@@ -79,6 +84,10 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w) {
     const size_t opc = take(sizeof(double2) * (size_t)nblk * DST_MAX_VEC);
     const size_t opr = take(sizeof(double) * (size_t)nblk);
     const size_t ocols = take(sizeof(double) * (size_t)COL_STRIDE * DST_MAX_VEC);
+    const size_t oZ = precond ? take(sizeof(float2) * (size_t)n * m) : 0;
+    const size_t opres = precond == DST_PRECOND_CN_SWEEP2 ? take(sizeof(float2) * (size_t)n) : 0;
+    const size_t opz2 = precond == DST_PRECOND_CN_SWEEP2 ? take(sizeof(float2) * (size_t)n) : 0;
+    const size_t osw = precond ? take(sweep_bytes) : 0;
     const size_t total = off;
     if (mesh->ws_bytes < total) {
         cudaFree(mesh->ws);
@@ -114,11 +123,15 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w) {
     w.partials_c = (double2 *)(base + opc);
     w.partials_r = (double *)(base + opr);
     w.cols = (double *)(base + ocols);
+    w.Z = precond ? (float2 *)(base + oZ) : nullptr;
+    w.pr = precond == DST_PRECOND_CN_SWEEP2 ? (float2 *)(base + opres) : nullptr;
+    w.pz2 = precond == DST_PRECOND_CN_SWEEP2 ? (float2 *)(base + opz2) : nullptr;
+    w.sweep_scratch = precond ? (void *)(base + osw) : nullptr;
     return DST_OK;
 }
 
 // Kernel classes reported in dst_solve_stats (index = DST_K_* in diracst.h).
-enum { K_APPLY64 = 0, K_APPLY32, K_CAST, K_PROJECT, K_UPDATE, K_SCALE, K_MISC, K_RHS, K_NCLASS };
+enum { K_APPLY64 = 0, K_APPLY32, K_CAST, K_PROJECT, K_UPDATE, K_SCALE, K_MISC, K_RHS, K_PRECOND, K_NCLASS };
 
 // Per-class accounting of launches, algorithmic bytes / flops and, when
 // profiling, device time from CUDA events recorded around each launch on the
@@ -257,6 +270,8 @@ struct Solver {
     int restarts = 0;
     int reorths = 0;
     int ortho = 0;           // 0: DGKS selective second pass, 1: always two passes, 2: one pass
+    int precond = 0;         // DST_PRECOND_*: flexible GMRES with the Crank-Nicolson sweep
+    SweepPlan plan;
     double resid_est = 0.0;
     Prof prof;
     CycleGraph graph;
@@ -283,10 +298,12 @@ struct Solver {
     int apply(int prec, const double2 *in, double2 *out) {
         const double n = (double)w.n;
         if (prec == DST_FP64)
-            return run(K_APPLY64, 1, 32.0 * n, 0.0, [&] { return dst_internal_apply(mesh, DST_FP64, in, out, s); });
+            return run(K_APPLY64, 1, 32.0 * n, dst_internal_apply_flops(mesh),
+                       [&] { return dst_internal_apply(mesh, DST_FP64, in, out, s); });
         int rc = run(K_CAST, 1, 24.0 * n, 0.0, [&] { return dst_k_cast_64_32(w.n, in, w.x32, s); });
         if (rc) return rc;
-        rc = run(K_APPLY32, 1, 16.0 * n, 0.0, [&] { return dst_internal_apply(mesh, DST_FP32, w.x32, w.y32, s); });
+        rc = run(K_APPLY32, 1, 16.0 * n, dst_internal_apply_flops(mesh),
+                 [&] { return dst_internal_apply(mesh, DST_FP32, w.x32, w.y32, s); });
         if (rc) return rc;
         return run(K_CAST, 1, 24.0 * n, 0.0, [&] { return dst_k_cast_32_64(w.n, w.y32, out, s); });
     }
@@ -527,6 +544,25 @@ struct Solver {
         return DST_OK;
     }
 
+    // z = M(v) with the Crank-Nicolson sweep; the second variant adds M(v - A M(v)),
+    // with tmp (a free FP32 vector: the next basis slot) holding A M(v).
+    int precondition(const float2 *v, float2 *z, float2 *tmp) {
+        const int64_t n = w.n;
+        const double dn = (double)n;
+        const double sweep_bytes = (plan.has_fft ? 48.0 : 40.0) * dn + (double)plan.table_bytes * plan.g.nt;
+        int rc = run(K_PRECOND, plan.has_fft ? 4 : 3, sweep_bytes, 0.0,
+                     [&] { return dst_sweep_apply(plan, n, v, z, s); });
+        if (rc || precond != DST_PRECOND_CN_SWEEP2) return rc;
+        if ((rc = run(K_APPLY32, 1, 16.0 * dn, dst_internal_apply_flops(mesh),
+                      [&] { return dst_internal_apply(mesh, DST_FP32, z, tmp, s); })))
+            return rc;
+        if ((rc = run(K_MISC, 1, 24.0 * dn, 2.0 * dn, [&] { return dst_k_sub_f32(n, v, tmp, w.pr, s); }))) return rc;
+        if ((rc = run(K_PRECOND, plan.has_fft ? 4 : 3, sweep_bytes, 0.0,
+                      [&] { return dst_sweep_apply(plan, n, w.pr, w.pz2, s); })))
+            return rc;
+        return run(K_MISC, 1, 24.0 * dn, 2.0 * dn, [&] { return dst_k_add_f32(n, w.pz2, z, s); });
+    }
+
     // The Arnoldi steps of one mixed cycle: a zeroed record per step, then per
     // step the FP32 apply, both Gram-Schmidt passes (the second gated on the
     // device) and the scaling, all on stream s.
@@ -550,9 +586,16 @@ struct Solver {
             double2 *c1 = reinterpret_cast<double2 *>(w.cols + (size_t)j * COL_STRIDE);
             double2 *c2 = c1 + DST_MAX_VEC;
             double *nr = w.cols + (size_t)j * COL_STRIDE + 4 * DST_MAX_VEC;
-            // FP32 apply straight from the hi plane of v_j into the hi plane of w
-            if ((rc = run(K_APPLY32, 1, 16.0 * dn, 0.0,
-                          [&] { return dst_internal_apply(mesh, DST_FP32, vj, wv, s); })))
+            // flexible GMRES: the operator is applied to z_j = M(v_j), kept in Z
+            const float2 *av = vj;
+            if (precond) {
+                float2 *zj = w.Z + (size_t)j * n;
+                if ((rc = precondition(vj, zj, wv))) return rc;
+                av = zj;
+            }
+            // FP32 apply straight from the hi plane of v_j (or z_j) into the hi plane of w
+            if ((rc = run(K_APPLY32, 1, 16.0 * dn, dst_internal_apply_flops(mesh),
+                          [&] { return dst_internal_apply(mesh, DST_FP32, av, wv, s); })))
                 return rc;
             if ((rc = run(K_PROJECT, 1, vb * dn * nv + 8.0 * dn, 8.0 * dn * nv, [&] {
                      return use_tma ? dst_k_project_tma(n, nv, Vd, wv, c1, w.partials_c, nblk_tma, s, nr + 3, nullptr,
@@ -659,8 +702,9 @@ struct Solver {
         }
         hs.solve(k, w.host, 1.0);
         DST_CUDA_TRY(cudaMemcpyAsync(w.h1, w.host, sizeof(double2) * k, cudaMemcpyHostToDevice, s));
+        const float2 *basis = precond ? w.Z : Vd;       // flexible GMRES: d = Z y
         if ((rc = run(K_UPDATE, 1, vb * dn * k + 32.0 * dn, 8.0 * dn * k,
-                      [&] { return dst_k_combine_df(n, k, Vd, w.h1, d, s, vlo); })))
+                      [&] { return dst_k_combine_df(n, k, basis, w.h1, d, s, vlo); })))
             return rc;
         ++restarts;
         return DST_OK;
@@ -787,6 +831,7 @@ extern "C" int dst_default_solve_opts(dst_solve_opts *o) {
     o->mixed_ortho = 2;
     o->method = 0;
     o->batch_cta_max = -1;
+    o->precond = DST_PRECOND_NONE;
     return DST_OK;
 }
 
@@ -802,8 +847,17 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     sv.nblk_proj = mixed && o.mixed_ortho == 2 ? std::min(dst_reduction_blocks(mesh->n_unknowns), 3 * 152)
                                                : dst_projection_blocks(mesh->n_unknowns);
     sv.ortho = o.ortho;
-    int rc = setup_workspace(mesh, o.method == 1 ? std::max(o.restart, 5) : o.restart, mixed, sv.w);
+    sv.precond = o.precond;
+    size_t sweep_bytes = 0;
+    if (o.precond) {
+        int rp = dst_sweep_plan(mesh, sv.plan);
+        if (rp) return rp;
+        sweep_bytes = dst_sweep_scratch_bytes(sv.plan, mesh->n_unknowns);
+    }
+    int rc = setup_workspace(mesh, o.method == 1 ? std::max(o.restart, 5) : o.restart, mixed, sv.w, o.precond,
+                             sweep_bytes);
     if (rc) return rc;
+    if (o.precond && (rc = dst_sweep_setup(mesh, sv.plan, sv.w.sweep_scratch, s))) return rc;
     // the mesh owns its page-locked record buffer (freed with the mesh), so
     // solves from short-lived threads leave no pinned memory behind
     if (!mesh->host_pinned) {
@@ -918,7 +972,8 @@ extern "C" int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, 
     if (!mesh || !psi || o.restart < 1 || o.restart > DST_MAX_VEC - 1 || o.max_iters < 0 || !(o.rtol >= 0) ||
         (o.mixed_precision && (!(o.inner_rtol > 0) || o.max_refine < 1)) || o.ortho < 0 || o.ortho > 2 ||
         o.mixed_ortho < 0 || o.mixed_ortho > 2 || o.inner_cycles < 0 || o.method < 0 || o.method > 1 ||
-        (o.method == 1 && o.mixed_precision)) {
+        (o.method == 1 && o.mixed_precision) || o.precond < 0 || o.precond > DST_PRECOND_CN_SWEEP2 ||
+        (o.precond && (!o.mixed_precision || o.mixed_ortho != 2 || o.inner_cycles != 1 || o.method != 0))) {
         rc = DST_ERR_ARG;
     } else if (!mesh->d_psi0) {
         rc = DST_ERR_STATE;

@@ -103,6 +103,14 @@ int dst_launch_rhs_d1(const OpParams &p, const double2 *psi0, double2 *b, cudaSt
 int dst_launch_rhs_d2(const OpParams &p, const double2 *psi0, double2 *b, cudaStream_t s);
 int dst_launch_rhs_d3(const OpParams &p, const double2 *psi0, double2 *b, cudaStream_t s);
 
+// Algorithmic floating-point operations of one operator apply: per complex
+// unknown, the sum-factorised evaluation (real flops, an FMA counting two):
+// x stencils M, C (8); in 2+1 the y pass on them (14), in 3+1 y (14) and z (20);
+// a potential's weighted mass field (10, +6 per further axis); the spin
+// combination (4 + 4 d) and the two time stencils (10).  Per unknown: 26 / 44 /
+// 68 in 1+1 / 2+1 / 3+1, plus 10 / 16 / 22 with a potential.
+double dst_internal_apply_flops(const dst_mesh *mesh);
+
 // Dispatch on the mesh dimension.
 int dst_internal_apply(const dst_mesh *mesh, int precision, const void *x, void *y, cudaStream_t s);
 int dst_internal_rhs(const dst_mesh *mesh, double2 *b, cudaStream_t s);

@@ -363,6 +363,12 @@ extern "C" int dst_set_initial_data(dst_mesh *mesh, const double *psi0) {
     return dst_internal_guard("dst_set_initial_data", [&] { return set_initial_data(mesh, psi0); });
 }
 
+double dst_internal_apply_flops(const dst_mesh *mesh) {
+    static const double base[4] = {0.0, 26.0, 44.0, 68.0}, pot[4] = {0.0, 10.0, 16.0, 22.0};
+    const double per = base[mesh->d] + (mesh->V.empty() ? 0.0 : pot[mesh->d]);
+    return per * (double)mesh->n_unknowns;
+}
+
 int dst_internal_apply(const dst_mesh *mesh, int precision, const void *x, void *y, cudaStream_t s) {
     OpParams p = dst_internal_params(mesh);
     switch (mesh->d) {

@@ -53,8 +53,10 @@ def test_single_rank_aggregate_and_replica_inputs():
     import bench
     import workloads as W
     assert bench.aggregate_timing(200.0, 1, 4) == (200.0, 4 / 0.2)
-    a, b = W.zb_2p1(n=16, nt=4, seed=bench.replica_seed(0)), W.zb_2p1(n=16, nt=4, seed=bench.replica_seed(1))
-    assert a.extra["phi"] != b.extra["phi"] and not np.allclose(a.psi0, b.psi0)
+    a = W.klein_3p1(n=8, nt=4, seed=bench.replica_seed(0))
+    b = W.klein_3p1(n=8, nt=4, seed=bench.replica_seed(1))
+    assert a.extra["p0"] != b.extra["p0"] and not np.allclose(a.psi0, b.psi0)
+    assert bench.headline_workload(0).extra["seed"] == 1
 
 
 def test_reference_arm_runs_on_rank_zero_only(capsys):

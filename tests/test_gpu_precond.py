@@ -1,0 +1,180 @@
+"""GPU Crank-Nicolson sweep preconditioner and flexible GMRES against the oracle.
+
+The sweep M = B^-1 S^-1 (oracle.precond.crank_nicolson_sweep, pinned on the CPU
+by tests/test_oracle_precond.py) runs on the GPU in FP32: a backward time scan,
+FFTs over the periodic axes, a march per frequency (2 x 2 / 4 x 4 recurrences,
+or block Thomas eliminations along a Dirichlet x axis), inverse FFTs.
+
+Tolerance of the sweep.  The oracle gets the same FP32-rounded input and works
+in FP64.  The GPU's error is FP32 rounding carried through ~N_t recurrence steps
+whose maps have norm about one (Crank-Nicolson is unitary on Hermitian K_s), the
+FFTs (~log2 n roundings) and the layer solves (condition number of Bd up to
+~10^2 on these meshes): eps32 x N_t x 10^2 ~ 1e-4 in the worst entry.  Checked:
+rel. L2 <= 1e-4, max |dz| <= 1e-3 max |z|.  A wrong sign, index or dropped term
+gives O(1).
+
+Flexible GMRES (Saad 1993) with the sweep, inside the mixed-precision
+refinement: the solution matches the oracle's exact one (LU) at the mixed
+tolerance 1e-8, the step count is close to the oracle's own FGMRES with the
+oracle's sweep and far below plain GMRES, and a few steps of the first cycle
+give the oracle FGMRES iterate to FP32 accuracy.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from _helpers import max_rel, oracle_mesh, rel_l2
+
+pytestmark = pytest.mark.gpu
+P, D = W.PERIODIC, W.DIRICHLET
+
+SWEEP_CASES = [
+    ("1p1_periodic", 1, [16, 1, 1, 6], [P], "const"),
+    ("1p1_periodic_odd", 1, [15, 1, 1, 7], [P], "none"),
+    ("2p1_periodic", 2, [8, 6, 1, 6], [P, P], "const"),
+    ("2p1_periodic_mixed_radix", 2, [24, 20, 1, 5], [P, P], "none"),
+    ("1p1_dirichlet", 1, [14, 1, 1, 6], [D], "x"),
+    ("2p1_dirichlet_x", 2, [9, 6, 1, 5], [D, P], "x"),
+    ("3p1_dirichlet_x", 3, [6, 4, 5, 4], [D, P, P], "x"),
+    ("3p1_dirichlet_x_larger", 3, [12, 8, 6, 5], [D, P, P], "none"),
+]
+
+
+def _workload(d, n_el, bc, vkind, seed):
+    w = W.random_mesh(d, n_el, bc, seed=seed, with_potential=False)
+    nel = [n_el[k] if k < d else 1 for k in range(3)]
+    rng = np.random.default_rng(seed + 1)
+    if vkind == "const":
+        w.V = np.full(nel[0] * nel[1] * nel[2], 0.7)
+    elif vkind == "x":
+        w.V = np.tile(rng.uniform(-0.5, 1.5, nel[0]), nel[1] * nel[2])
+    return w
+
+
+def _oracle_sweep(w):
+    from oracle import operator as OOP, precond as PC
+    om = oracle_mesh(w)
+    A, b = OOP.split(om, OOP.assemble(om, w.m, w.V), w.psi0)
+    per = om.n_spatial_nodes * om.nc
+    Mc = PC.crank_nicolson_sweep(A.tocsr(), om.nt, per)[0]
+    return om, A.tocsr(), b, Mc
+
+
+@pytest.mark.parametrize("name,d,n_el,bc,vkind", SWEEP_CASES)
+def test_sweep_matches_oracle(name, d, n_el, bc, vkind):
+    import torch
+    from paper_2103_14588_gb300 import binding as B
+    w = _workload(d, n_el, bc, vkind, seed=80 + d)
+    om, A, b, Mc = _oracle_sweep(w)
+    v = W.random_complex(om.n_unknowns, 90 + d).astype(np.complex64)
+    ref = Mc(v.astype(np.complex128))
+    with B.Mesh.from_workload(w) as mesh:
+        vd = torch.from_numpy(v).cuda()
+        zd = torch.full_like(vd, complex("nan+nanj"))
+        B.dst_precond_apply(mesh.handle, B.DST_PRECOND_CN_SWEEP, vd, zd)
+        torch.cuda.synchronize()
+        got = zd.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert rel_l2(got, ref) <= 1e-4, rel_l2(got, ref)
+    assert max_rel(got, ref) <= 1e-3
+
+
+def test_sweep_rejects_meshes_it_does_not_cover():
+    import torch
+    from paper_2103_14588_gb300 import binding as B
+    cases = [(2, [6, 5, 1, 4], [W.OPEN, P]), (2, [6, 5, 1, 4], [D, D]), (2, [6, 5, 1, 4], [P, D]),
+             (3, [4, 4, 4, 3], [P, P, P])]
+    for d, n_el, bc in cases:
+        w = W.random_mesh(d, n_el, bc, seed=1, with_potential=False)
+        with B.Mesh.from_workload(w) as mesh:
+            v = torch.zeros(mesh.n_unknowns, dtype=torch.complex64, device="cuda")
+            z = torch.zeros_like(v)
+            with pytest.raises(B.DstError) as e:
+                B.dst_precond_apply(mesh.handle, B.DST_PRECOND_CN_SWEEP, v, z)
+            assert e.value.code == B.DST_ERR_ARG
+
+
+FGMRES_CASES = [
+    ("plane_wave_32", lambda: W.plane_wave_1p1(n=32)),
+    ("zb_2p1_16", lambda: W.zb_2p1(n=16, nt=16)),
+    ("klein_3p1_8", lambda: W.klein_3p1(n=8, nt=8, p0=1.05)),
+]
+
+
+@pytest.mark.parametrize("name,make", FGMRES_CASES)
+def test_preconditioned_solve_matches_lu(name, make):
+    import torch
+    from oracle import solvers as OS
+    from paper_2103_14588_gb300 import binding as B
+    w = make()
+    om, A, b, Mc = _oracle_sweep(w)
+    ref = OS.sparse_solve(A, b)
+    f = OS.fgmres(lambda v: A @ v, b, Mc, restart=30, rtol=1e-8, maxiter=20000)
+    with B.Mesh.from_workload(w) as mesh:
+        psi = torch.zeros(mesh.n_unknowns, dtype=torch.complex128, device="cuda")
+        base = {"restart": 30, "rtol": 1e-10, "max_iters": 20000, "mixed_precision": 1, "ortho": 0}
+        st = B.dst_solve(mesh.handle, dict(base, precond=B.DST_PRECOND_CN_SWEEP), psi)
+        torch.cuda.synchronize()
+        x = psi.cpu().numpy()
+        st8 = B.dst_solve(mesh.handle, dict(base, rtol=1e-8, precond=B.DST_PRECOND_CN_SWEEP), psi)
+        st0 = B.dst_solve(mesh.handle, dict(base, rtol=1e-8), psi)
+        torch.cuda.synchronize()
+    assert st["status"] == 0, st
+    assert rel_l2(x, ref) <= 1e-8
+    # the sweep cuts the steps as the oracle's own FGMRES says
+    assert st8["status"] == 0 and f.converged
+    assert st8["iters"] <= 1.5 * f.iters + 10, (st8["iters"], f.iters)
+    assert st8["iters"] * 3 <= st0["iters"], (st8["iters"], st0["iters"])
+
+
+def test_first_cycle_iterate_matches_oracle_fgmres():
+    """Same flexible Krylov method from x_0 = 0: after 8 steps the iterates agree to FP32 accuracy."""
+    import torch
+    from oracle import solvers as OS
+    from paper_2103_14588_gb300 import binding as B
+    w = W.zb_2p1(n=16, nt=16)
+    om, A, b, Mc = _oracle_sweep(w)
+    f = OS.fgmres(lambda v: A @ v, b, Mc, restart=30, rtol=1e-14, maxiter=8)
+    with B.Mesh.from_workload(w) as mesh:
+        psi = torch.zeros(mesh.n_unknowns, dtype=torch.complex128, device="cuda")
+        st = B.dst_solve(mesh.handle, {"restart": 30, "rtol": 1e-14, "max_iters": 8, "mixed_precision": 1,
+                                       "ortho": 1, "precond": B.DST_PRECOND_CN_SWEEP}, psi)
+        torch.cuda.synchronize()
+        x = psi.cpu().numpy()
+    assert st["iters"] == 8
+    assert rel_l2(x, f.x) <= 1e-4, rel_l2(x, f.x)
+
+
+def test_two_sweeps_per_step():
+    """M2(v) = M(v) + M(v - A M(v)): fewer steps than one sweep, same solution."""
+    import torch
+    from oracle import solvers as OS
+    from paper_2103_14588_gb300 import binding as B
+    w = W.zb_2p1(n=16, nt=16)
+    om, A, b, Mc = _oracle_sweep(w)
+    ref = OS.sparse_solve(A, b)
+    M2 = lambda v: Mc(v) + Mc(v - A @ Mc(v))          # noqa: E731
+    f2 = OS.fgmres(lambda v: A @ v, b, M2, restart=30, rtol=1e-8, maxiter=5000)
+    with B.Mesh.from_workload(w) as mesh:
+        psi = torch.zeros(mesh.n_unknowns, dtype=torch.complex128, device="cuda")
+        base = {"restart": 30, "rtol": 1e-8, "max_iters": 5000, "mixed_precision": 1}
+        s1 = B.dst_solve(mesh.handle, dict(base, precond=B.DST_PRECOND_CN_SWEEP), psi)
+        s2 = B.dst_solve(mesh.handle, dict(base, precond=B.DST_PRECOND_CN_SWEEP2), psi)
+        torch.cuda.synchronize()
+        x = psi.cpu().numpy()
+    assert s2["status"] == 0 and rel_l2(x, ref) <= 1e-7
+    assert s2["iters"] < s1["iters"]
+    assert s2["iters"] <= 1.5 * f2.iters + 10, (s2["iters"], f2.iters)
+
+
+def test_precond_option_validation():
+    import torch
+    from paper_2103_14588_gb300 import binding as B
+    w = W.plane_wave_1p1(n=16)
+    with B.Mesh.from_workload(w) as mesh:
+        psi = torch.zeros(mesh.n_unknowns, dtype=torch.complex128, device="cuda")
+        for bad in ({"precond": 1, "mixed_precision": 0}, {"precond": 1, "mixed_precision": 1, "mixed_ortho": 0},
+                    {"precond": 3, "mixed_precision": 1}):
+            with pytest.raises(B.DstError) as e:
+                B.dst_solve(mesh.handle, bad, psi)
+            assert e.value.code == B.DST_ERR_ARG
