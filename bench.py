@@ -415,6 +415,50 @@ def apply_figures(torch, B, mesh_obj, st_prof, hbm):
     return out
 
 
+def run_precond_bench(torch, B):
+    """Flexible GMRES with the Crank-Nicolson sweep, and with the sweep plus the learned
+    U-Net correction (trained here on pairs generated on the GPU), against the plain
+    mixed solve, on the 2+1 Zitterbewegung packet at 48^3 (where the sweep preconditions)
+    and at the bench size 96^3 (where its quality is gone: ||A M v - v|| ~ ||v||)."""
+    import numpy as _np
+    out = {}
+    base = {"restart": RESTART, "rtol": RTOL, "max_iters": 2000, "mixed_precision": 1, "inner_rtol": INNER_RTOL}
+    for n in (48, 96):
+        w = W.zb_2p1(n=n, nt=n)
+        rec = {"unknowns": None}
+        with B.Mesh.from_workload(w) as m:
+            rec["unknowns"] = m.n_unknowns
+            psi = torch.zeros(m.n_unknowns, dtype=torch.complex128, device="cuda")
+            runs = [("plain", dict(base, ortho=ORTHO)), ("cn_sweep", dict(base, precond=B.DST_PRECOND_CN_SWEEP))]
+            net = None
+            if n == 48:
+                net = B.UNet(m.handle)
+                from_zero = net.get_params()
+                rng = _np.random.default_rng(3)
+                # He-normal hidden layers, zero output layer: training starts from the sweep itself
+                params = from_zero.copy()
+                params[:] = rng.standard_normal(params.size).astype(_np.float32) * 0.05
+                params[-(2 * m.ncomp * 16 + 2 * m.ncomp):] = 0.0
+                net.set_params(params)
+                t0 = time.perf_counter()
+                losses = net.train(m.handle, steps=300, lr=5e-4, seed=17)
+                rec["training"] = {"steps": 300, "seconds": time.perf_counter() - t0,
+                                   "loss_first_20": float(_np.mean(losses[:20])),
+                                   "loss_last_20": float(_np.mean(losses[-20:]))}
+                B.dst_set_learned_precond(m.handle, net)
+                runs.append(("cn_sweep_learned", dict(base, precond=B.DST_PRECOND_CN_LEARNED)))
+            for name, o in runs:
+                B.dst_solve(m.handle, dict(o, max_iters=60), psi)
+                t, st = timed_solve(torch, B, m.handle, o, psi)
+                rec[name] = {"time_s": t, "iters": st["iters"], "status": st["status"],
+                             "rel_resid_true": st["rel_resid_true"]}
+            if net is not None:
+                B.dst_set_learned_precond(m.handle, None)
+                net.close()
+        out["zb_2p1_%d" % n] = rec
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,6 +467,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve throughput cases")
+    ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned-solve comparison")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed solves (no FP64 comparisons, second workload, applies)")
     ap.add_argument("--ncu-case", choices=NCU_CASES, help="run one small case for an ncu capture and exit")
@@ -587,6 +632,7 @@ def main():
            "d2h_bytes_per_step": int(n * 16)}
 
     batch = None if args.no_batch else run_batch_bench(torch, B)
+    precond = None if args.no_precond else run_precond_bench(torch, B)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -616,6 +662,7 @@ def main():
                                "fp64": B.dst_get_apply_variant(mesh, B.DST_FP64)[0]},
         "kernels": kernels,
         "batch": batch,
+        "preconditioners": precond,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -218,9 +218,9 @@ typedef struct {
                                FP32 products and sums, FP64 reductions; needs inner_cycles = 1),
                                1 = native FP64 (FP64 basis),
                                2 = FP32-stored basis (8 B per entry, half the traffic of 0) with
-                               exact FP32 products and compensated sums: inner products and
-                               updates of the stored values carry about 45 bits relative to the
-                               sum of the terms' magnitudes, each new basis vector is rounded to
+                               exact FP32 products and compensated sums: inner products of the
+                               stored values err by about 2^-40 of ||v|| ||w||, updates are
+                               rounded to FP32 once, each new basis vector is rounded to
                                FP32 once; from 4M unknowns the projection is fed by bulk
                                asynchronous copies (needs inner_cycles = 1) */
     int method;             /* Krylov method: 0 = restarted GMRES(restart) (default),
@@ -235,7 +235,8 @@ typedef struct {
                                cycle's correction is Z y.  Needs mixed_precision = 1,
                                mixed_ortho = 2, inner_cycles = 1, method = 0.
                                DST_PRECOND_CN_SWEEP2 applies the sweep twice per step,
-                               z = M v + M (v - A M v).  dst_solve_batch honours it for the meshes
+                               z = M v + M (v - A M v); DST_PRECOND_CN_LEARNED adds the
+                               network attached by dst_set_learned_precond to the sweep.  dst_solve_batch honours it for the meshes
                                it solves one by one and ignores it in the persistent kernel */
 } dst_solve_opts;
 
@@ -378,6 +379,23 @@ enum { DST_TEST_WAIT_LIMIT = 1, DST_TEST_FAIL_ALLOC = 2 };
 DST_API int dst_testing_set(int hook, int64_t value);
 
 /*
+ * Testing access to the Gram-Schmidt kernels of the mixed solve on an
+ * FP32-stored Krylov basis (Sec. 2.2's GMRES; the arithmetic is the library's):
+ * V holds nvec DEVICE FP32 complex vectors (float pairs) of length n (n even,
+ * 1 <= nvec <= 64) one after another, w one more.
+ *   mode 0: h = V^H w by the register-fed projection (h: DEVICE nvec FP64 complex);
+ *   mode 1: the same by the bulk-copy fed projection;
+ *   mode 2: w <- w - V h (h: DEVICE FP64 complex input), rounded to FP32 once,
+ *           and *nrm2 (DEVICE double) = ||w||^2 of the stored result.
+ * Products are exact and sums compensated: the error of h_j is about 2^-40 of
+ * ||v_j|| ||w|| (measured with unit basis vectors).  Takes stream-ordered
+ * scratch; mode 1 synchronises the stream.  Errors: DST_ERR_ARG, DST_ERR_OOM,
+ * DST_ERR_CUDA (a bulk-copy wait that gave up).
+ */
+DST_API int dst_testing_fp32_arnoldi(int mode, int64_t n, int nvec, const void *V, void *w, void *h, void *nrm2,
+                                     void *stream);
+
+/*
  * Right preconditioners for flexible GMRES (dst_solve_opts.precond).  The paper
  * names none; its conclusion (Sec. 5) asks for one and points at decomposing
  * the time direction.
@@ -397,8 +415,74 @@ DST_API int dst_testing_set(int hook, int64_t value);
  * the factors, 32 NC^2 bytes per x node and frequency, on Dirichlet-x meshes).
  * Errors: DST_ERR_ARG (kind, mesh not covered), DST_ERR_OOM, DST_ERR_CUDA.
  */
-enum { DST_PRECOND_NONE = 0, DST_PRECOND_CN_SWEEP = 1, DST_PRECOND_CN_SWEEP2 = 2 };
+enum { DST_PRECOND_NONE = 0, DST_PRECOND_CN_SWEEP = 1, DST_PRECOND_CN_SWEEP2 = 2, DST_PRECOND_CN_LEARNED = 3 };
 DST_API int dst_precond_apply(const dst_mesh *mesh, int kind, const void *v, void *z, void *stream);
+
+/*
+ * Energy per unknown time layer, E(t) = int psi^dagger H psi dx with the free
+ * Dirac Hamiltonian H = alpha . p + beta m applied spectrally (the energy of
+ * Sec. 4.1's conservation study; the paper does not define its E(t), this is
+ * one reading of it): FP64 FFT of every layer, then (prod_k h_k) / N times the
+ * sum over frequencies of psi^ dagger H(p) psi^, p_k = 2 pi q_k / (n_k h_k) with
+ * q_k the signed frequency.  Meshes whose spatial axes are all periodic (axes
+ * up to 4096 nodes).  psi: DEVICE FP64 solution (n_unknowns complex); out:
+ * DEVICE array of N_t doubles.  Takes stream-ordered scratch of one (3+1: two)
+ * FP64 vectors.  Errors: DST_ERR_ARG (a non-periodic axis), DST_ERR_OOM,
+ * DST_ERR_CUDA.
+ */
+DST_API int dst_energy(const dst_mesh *mesh, const void *psi, void *out, void *stream);
+
+/*
+ * Learned correction of the sweep (DST_PRECOND_CN_LEARNED; no counterpart in
+ * the paper, whose conclusion (Sec. 5) asks for a preconditioner):
+ *     M(v) = M_CN(v) + s U(rho / s),   rho = v - A M_CN(v),  s = ||rho||,
+ * with U a convolutional U-Net on the spacetime node grid (t, [z], [y], x) of the
+ * unknowns, 2 NC channels (Re, Im of each spinor component, i.e. the FP32
+ * complex unknown vector read as [node][channel] floats).  Layers, in order
+ * (conv3: kernel 3 in every grid axis, zero padding keeping the size; conv1:
+ * kernel 1; every convolution has a bias):
+ *   e1a conv3 C->16 ReLU, e1b conv3 16->16 ReLU (=s1), mean-pool 2;
+ *   e2a conv3 16->32 ReLU, e2b conv3 32->32 ReLU (=s2), mean-pool 2;
+ *   e3a conv3 32->64 ReLU, e3b conv3 64->64 ReLU, nearest upsample;
+ *   u2p conv1 64->32, + s2, u2c conv3 32->32 ReLU, nearest upsample;
+ *   u1p conv1 32->16, + s1, u1c conv3 16->16 ReLU; out conv1 16->C.
+ * (pooling counts cells past an odd end as zero.)  Convolutions run on BF16
+ * tensor cores with FP32 accumulation; parameters are FP32, rounded to BF16.
+ * The flat parameter vector holds, per layer in this order, the weight
+ * (c_out, c_in, kernel offsets row-major over the grid axes) and then the bias.
+ *
+ * dst_unet_create: a network for the mesh's grid, parameters zero; DEVICE
+ *   memory for parameters, Adam moments, activations and their gradients.
+ * dst_unet_num_params / set_params / get_params: the flat FP32 vector (HOST).
+ * dst_unet_forward: y = ||x|| U(x / ||x||), x and y DEVICE FP32 complex vectors
+ *   of the mesh's n_unknowns entries (distinct).
+ * dst_unet_loss_grad: for DEVICE x, target: L = ||U(x^) - t^||^2 / ||t^||^2 with
+ *   x^ = x / ||x||, t^ = target / ||x||; *loss (HOST) and the gradient of L with
+ *   respect to every parameter (HOST, num_params floats; either may be NULL).
+ *   Synchronises the stream.
+ * dst_unet_train: `steps` Adam steps (learning rate lr, beta 0.9 / 0.999) on
+ *   pairs the method generates on the GPU: e standard normal (splitmix64 of
+ *   seed and index), r = A e, z = M_CN(r), input rho = r - A z, target e - z;
+ *   loss per step into loss_host (HOST, `steps` floats, may be NULL).  The mesh
+ *   must be one the sweep covers.  Synchronises the stream.
+ * dst_set_learned_precond: use `net` (NULL: none) in solves of this mesh with
+ *   precond = DST_PRECOND_CN_LEARNED.  The mesh does not own it; solves that
+ *   share one network must not overlap.
+ * Errors: DST_ERR_ARG (a network built for another mesh, bad sizes),
+ * DST_ERR_OOM, DST_ERR_CUDA.
+ */
+typedef struct dst_unet dst_unet;
+DST_API int dst_unet_create(const dst_mesh *mesh, dst_unet **out);
+DST_API int dst_unet_destroy(dst_unet *net);
+DST_API int dst_unet_num_params(const dst_unet *net, int64_t *n);
+DST_API int dst_unet_set_params(dst_unet *net, const float *params);
+DST_API int dst_unet_get_params(const dst_unet *net, float *params);
+DST_API int dst_unet_forward(dst_unet *net, const void *x, void *y, void *stream);
+DST_API int dst_unet_loss_grad(dst_unet *net, const void *x, const void *target, double *loss, float *grad,
+                               void *stream);
+DST_API int dst_unet_train(dst_unet *net, dst_mesh *mesh, int steps, float lr, uint64_t seed, float *loss,
+                           void *stream);
+DST_API int dst_set_learned_precond(dst_mesh *mesh, dst_unet *net);
 
 /* Static, human-readable name of a status code. */
 DST_API const char *dst_status_string(int status);

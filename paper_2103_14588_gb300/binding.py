@@ -21,7 +21,7 @@ DST_ERR_ARG, DST_ERR_OOM, DST_ERR_CUDA, DST_ERR_NAN, DST_ERR_STATE = -1, -2, -3,
 DST_BC_PERIODIC, DST_BC_OPEN, DST_BC_DIRICHLET = 0, 1, 2
 DST_FP64, DST_FP32 = 0, 1
 DST_TEST_WAIT_LIMIT, DST_TEST_FAIL_ALLOC = 1, 2
-DST_PRECOND_NONE, DST_PRECOND_CN_SWEEP, DST_PRECOND_CN_SWEEP2 = 0, 1, 2
+DST_PRECOND_NONE, DST_PRECOND_CN_SWEEP, DST_PRECOND_CN_SWEEP2, DST_PRECOND_CN_LEARNED = 0, 1, 2, 3
 
 EXPORTED = (
     "dst_create_mesh", "dst_destroy_mesh", "dst_mesh_sizes", "dst_set_mass", "dst_set_potential",
@@ -29,7 +29,10 @@ EXPORTED = (
     "dst_arnoldi_update", "dst_default_solve_opts", "dst_solve", "dst_status_string",
     "dst_last_error_detail", "dst_arnoldi_project_noalloc", "dst_observables", "dst_solve_batch",
     "dst_tune_apply", "dst_set_apply_variant", "dst_get_apply_variant", "dst_testing_set",
-    "dst_set_boundary_data", "dst_precond_apply",
+    "dst_set_boundary_data", "dst_precond_apply", "dst_energy",
+    "dst_unet_create", "dst_unet_destroy", "dst_unet_num_params", "dst_unet_set_params", "dst_unet_get_params",
+    "dst_unet_forward", "dst_unet_loss_grad", "dst_unet_train", "dst_set_learned_precond",
+    "dst_testing_fp32_arnoldi",
 )
 
 
@@ -101,6 +104,17 @@ def _load():
         "dst_last_error_detail": (ctypes.c_char_p, []),
         "dst_testing_set": (c_int, [c_int, i64]),
         "dst_precond_apply": (c_int, [vp, c_int, vp, vp, vp]),
+        "dst_energy": (c_int, [vp, vp, vp, vp]),
+        "dst_unet_create": (c_int, [vp, P(vp)]),
+        "dst_unet_destroy": (c_int, [vp]),
+        "dst_unet_num_params": (c_int, [vp, P(i64)]),
+        "dst_unet_set_params": (c_int, [vp, vp]),
+        "dst_unet_get_params": (c_int, [vp, vp]),
+        "dst_unet_forward": (c_int, [vp, vp, vp, vp]),
+        "dst_unet_loss_grad": (c_int, [vp, vp, vp, P(c_double), vp, vp]),
+        "dst_unet_train": (c_int, [vp, vp, c_int, ctypes.c_float, ctypes.c_uint64, vp, vp]),
+        "dst_set_learned_precond": (c_int, [vp, vp]),
+        "dst_testing_fp32_arnoldi": (c_int, [c_int, i64, c_int, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -290,6 +304,16 @@ def dst_testing_set(hook, value):
     return _check(_lib.dst_testing_set(int(hook), int(value)), "dst_testing_set")
 
 
+def dst_energy(mesh, psi, out, stream=None):
+    """Energy per time layer of a solution (out: N_t float64 CUDA tensor); periodic meshes."""
+    import torch
+    ns, nu, nc = dst_mesh_sizes(mesh)
+    nt = nu // (ns * nc)
+    pp = _dev_ptr(psi, torch.complex128, nu, "psi")
+    po = _dev_ptr(out, torch.float64, nt, "out")
+    return _check(_lib.dst_energy(mesh, pp, po, _stream(stream, psi, out)), "dst_energy")
+
+
 def dst_default_solve_opts():
     o = dst_solve_opts()
     _check(_lib.dst_default_solve_opts(ctypes.byref(o)), "dst_default_solve_opts")
@@ -356,6 +380,76 @@ def dst_solve_batch(meshes, opts, psis, stream=None):
     if rc < 0 and rc not in (DST_ERR_NAN,):
         _check(rc, "dst_solve_batch")
     return rc, [s_.as_dict() for s_ in sts]
+
+
+class UNet:
+    """Owning wrapper of a dst_unet handle (the learned correction of the sweep preconditioner)."""
+
+    def __init__(self, mesh_handle):
+        self.handle = None
+        out = ctypes.c_void_p()
+        _check(_lib.dst_unet_create(mesh_handle, ctypes.byref(out)), "dst_unet_create")
+        self.handle = out.value
+        n = ctypes.c_int64()
+        _check(_lib.dst_unet_num_params(self.handle, ctypes.byref(n)), "dst_unet_num_params")
+        self.num_params = n.value
+
+    def set_params(self, params):
+        arr = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        if arr.size != self.num_params:
+            raise ValueError("need %d parameters, got %d" % (self.num_params, arr.size))
+        _check(_lib.dst_unet_set_params(self.handle, arr.ctypes.data), "dst_unet_set_params")
+
+    def get_params(self):
+        arr = np.empty(self.num_params, dtype=np.float32)
+        _check(_lib.dst_unet_get_params(self.handle, arr.ctypes.data), "dst_unet_get_params")
+        return arr
+
+    def forward(self, x, y, stream=None):
+        import torch
+        px = _dev_ptr(x, torch.complex64, None, "x")
+        py = _dev_ptr(y, torch.complex64, None, "y")
+        _check(_lib.dst_unet_forward(self.handle, px, py, _stream(stream, x, y)), "dst_unet_forward")
+
+    def loss_grad(self, x, target, stream=None):
+        """(loss, gradient as a float32 numpy array); synchronises."""
+        import torch
+        px = _dev_ptr(x, torch.complex64, None, "x")
+        pt = _dev_ptr(target, torch.complex64, None, "target")
+        loss = ctypes.c_double()
+        g = np.empty(self.num_params, dtype=np.float32)
+        _check(_lib.dst_unet_loss_grad(self.handle, px, pt, ctypes.byref(loss), g.ctypes.data,
+                                       _stream(stream, x, target)), "dst_unet_loss_grad")
+        return loss.value, g
+
+    def train(self, mesh_handle, steps, lr, seed, stream=0):
+        losses = np.empty(max(steps, 1), dtype=np.float32)
+        _check(_lib.dst_unet_train(self.handle, mesh_handle, int(steps), float(lr), int(seed) & ((1 << 64) - 1),
+                                   losses.ctypes.data, stream if isinstance(stream, int) else stream.cuda_stream),
+               "dst_unet_train")
+        return losses[:steps]
+
+    def close(self):
+        if self.handle:
+            _lib.dst_unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def dst_set_learned_precond(mesh, net):
+    return _check(_lib.dst_set_learned_precond(mesh, net.handle if net is not None else None),
+                  "dst_set_learned_precond")
 
 
 class Mesh:

@@ -1,8 +1,9 @@
 // Operator apply and right-hand side instantiated for 3+1 dimensions (NC = 4).
 // A general per-element potential takes the shared-memory kernel of
 // apply_impl.cuh; x-only or vanishing potentials take the pipelined kernel of
-// apply_pipe.cuh.
-#include "apply_pipe.cuh"
+// apply_pipe.cuh, or on meshes without open axes the z-column kernel of
+// apply_zblk.cuh (tile variant 1).
+#include "apply_zblk.cuh"
 
 int dst_launch_apply_d3(const OpParams &p, int precision, const void *x, void *y, cudaStream_t s) {
     if (precision == DST_FP64) {

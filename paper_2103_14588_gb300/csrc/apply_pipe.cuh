@@ -567,13 +567,22 @@ int launch_apply_pipe_v(const OpParams &p, const typename C2<T>::type *x, typena
     return DST_OK;
 }
 
-// Number of tile variants per spatial dimension.
-constexpr int pipe_tile_variants(int d) { return d == 3 ? 1 : 3; }
+// Number of tile variants per spatial dimension (3+1: the one-output-per-thread
+// tiles of this file, and the z-columns of apply_zblk.cuh).
+constexpr int pipe_tile_variants(int d) { return d == 3 ? 2 : 3; }
+
+template <typename T, int RZ>
+int launch_apply_zblk(const OpParams &p, const typename C2<T>::type *x, typename C2<T>::type *y, cudaStream_t s);
 
 // Launch with the tile variant the parameters carry for this precision.
 template <int D, int NC, typename T>
 int launch_apply_pipe(const OpParams &p, const typename C2<T>::type *x, typename C2<T>::type *y, cudaStream_t s) {
     const int tv = p.tile_variant[sizeof(T) == 4 ? DST_FP32 : DST_FP64];
+    if constexpr (D == 3) {
+        bool all_std = true;
+        for (int k = 0; k < 3; ++k) all_std = all_std && p.ax[k].bc != DST_BC_OPEN;
+        if (tv == 1 && all_std && p.vmode != 1) return launch_apply_zblk<T, sizeof(T) == 4 ? 4 : 2>(p, x, y, s);
+    }
     if (D == 3 || tv <= 0) return launch_apply_pipe_v<D, NC, T, 0>(p, x, y, s);
     if constexpr (D < 3) {
         if (tv == 1) return launch_apply_pipe_v<D, NC, T, 1>(p, x, y, s);

@@ -26,6 +26,8 @@
 // products are still exact (TwoProd) and the sums compensated, so inner
 // products and updates keep FP64-class accuracy with respect to the stored
 // values; updated vectors are rounded to FP32 once.
+#include <algorithm>
+
 #include "blas.h"
 #include "df_arith.cuh"
 #include "tma.cuh"
@@ -897,4 +899,52 @@ int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double
     else combine_df_kernel<false><<<df_stream_blocks(n), DF_THREADS, 0, s>>>(n, k, V, y, x);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
+}
+
+// ---- testing entry point: the Gram-Schmidt kernels of the mixed solve -----------
+
+extern "C" int dst_testing_fp32_arnoldi(int mode, int64_t n, int nvec, const void *V, void *w, void *h, void *nrm2,
+                                        void *stream) {
+    if (mode < 0 || mode > 2 || n < 2 || (n & 1) || nvec < 1 || nvec > DST_MAX_VEC || !V || !w || !h ||
+        (mode == 2 && !nrm2)) {
+        dst_internal_set_error_detail("dst_testing_fp32_arnoldi: bad mode, size (n even >= 2, 1 <= nvec <= 64) "
+                                      "or pointer");
+        return DST_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nblk_reg = std::min(dst_reduction_blocks(n), 3 * 152);
+    const int nblk = mode == 1 ? dst_tma_projection_blocks(n) : (mode == 2 ? dst_reduction_blocks(n) : nblk_reg);
+    const size_t pbytes = sizeof(double2) * (size_t)nblk * (nvec + 1);
+    char *scr = nullptr;
+    if (cudaMallocAsync((void **)&scr, pbytes + 256 + 256, s) != cudaSuccess) {
+        cudaGetLastError();
+        return DST_ERR_OOM;
+    }
+    double2 *partials = (double2 *)scr;
+    unsigned *ticket = (unsigned *)(scr + ((pbytes + 255) & ~(size_t)255));
+    double *err = (double *)(ticket + 8);
+    int rc = DST_OK;
+    if (cudaMemsetAsync(ticket, 0, 64, s) != cudaSuccess) rc = DST_ERR_CUDA;
+    if (rc == DST_OK) {
+        if (mode == 0)
+            rc = dst_k_project_df(n, nvec, (const float2 *)V, (const float2 *)w, true, (double2 *)h, partials, nblk, s,
+                                  nullptr, nullptr, nullptr, ticket, false);
+        else if (mode == 1)
+            rc = dst_k_project_tma(n, nvec, (const float2 *)V, (const float2 *)w, (double2 *)h, partials, nblk, s,
+                                   nullptr, nullptr, ticket, err);
+        else
+            rc = dst_k_update_df(n, nvec, (const float2 *)V, (const double2 *)h, (float2 *)w, true, (double *)nrm2,
+                                 (double *)partials, nblk, s, nullptr, nullptr, ticket + 1, false);
+    }
+    double e = 0.0;
+    if (rc == DST_OK && mode == 1 &&
+        (cudaMemcpyAsync(&e, err, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess))
+        rc = DST_ERR_CUDA;
+    cudaFreeAsync(scr, s);
+    if (rc == DST_OK && e != 0.0) {
+        dst_internal_set_error_detail("dst_testing_fp32_arnoldi: a bulk-copy wait of the projection timed out");
+        rc = DST_ERR_CUDA;
+    }
+    return rc;
 }

@@ -85,7 +85,7 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w, int precond
     const size_t opr = take(sizeof(double) * (size_t)nblk);
     const size_t ocols = take(sizeof(double) * (size_t)COL_STRIDE * DST_MAX_VEC);
     const size_t oZ = precond ? take(sizeof(float2) * (size_t)n * m) : 0;
-    const size_t opres = precond == DST_PRECOND_CN_SWEEP2 ? take(sizeof(float2) * (size_t)n) : 0;
+    const size_t opres = precond >= DST_PRECOND_CN_SWEEP2 ? take(sizeof(float2) * (size_t)n) : 0;
     const size_t opz2 = precond == DST_PRECOND_CN_SWEEP2 ? take(sizeof(float2) * (size_t)n) : 0;
     const size_t osw = precond ? take(sweep_bytes) : 0;
     const size_t total = off;
@@ -124,7 +124,7 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w, int precond
     w.partials_r = (double *)(base + opr);
     w.cols = (double *)(base + ocols);
     w.Z = precond ? (float2 *)(base + oZ) : nullptr;
-    w.pr = precond == DST_PRECOND_CN_SWEEP2 ? (float2 *)(base + opres) : nullptr;
+    w.pr = precond >= DST_PRECOND_CN_SWEEP2 ? (float2 *)(base + opres) : nullptr;
     w.pz2 = precond == DST_PRECOND_CN_SWEEP2 ? (float2 *)(base + opz2) : nullptr;
     w.sweep_scratch = precond ? (void *)(base + osw) : nullptr;
     return DST_OK;
@@ -552,11 +552,13 @@ struct Solver {
         const double sweep_bytes = (plan.has_fft ? 48.0 : 40.0) * dn + (double)plan.table_bytes * plan.g.nt;
         int rc = run(K_PRECOND, plan.has_fft ? 4 : 3, sweep_bytes, 0.0,
                      [&] { return dst_sweep_apply(plan, n, v, z, s); });
-        if (rc || precond != DST_PRECOND_CN_SWEEP2) return rc;
+        if (rc || precond == DST_PRECOND_CN_SWEEP) return rc;
         if ((rc = run(K_APPLY32, 1, 16.0 * dn, dst_internal_apply_flops(mesh),
                       [&] { return dst_internal_apply(mesh, DST_FP32, z, tmp, s); })))
             return rc;
         if ((rc = run(K_MISC, 1, 24.0 * dn, 2.0 * dn, [&] { return dst_k_sub_f32(n, v, tmp, w.pr, s); }))) return rc;
+        if (precond == DST_PRECOND_CN_LEARNED)        // z += s U(rho / s), rho = v - A M_CN(v)
+            return run(K_PRECOND, 30, 0.0, 0.0, [&] { return dst_internal_unet_correct(mesh->unet, w.pr, z, s); });
         if ((rc = run(K_PRECOND, plan.has_fft ? 4 : 3, sweep_bytes, 0.0,
                       [&] { return dst_sweep_apply(plan, n, w.pr, w.pz2, s); })))
             return rc;
@@ -972,7 +974,8 @@ extern "C" int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, 
     if (!mesh || !psi || o.restart < 1 || o.restart > DST_MAX_VEC - 1 || o.max_iters < 0 || !(o.rtol >= 0) ||
         (o.mixed_precision && (!(o.inner_rtol > 0) || o.max_refine < 1)) || o.ortho < 0 || o.ortho > 2 ||
         o.mixed_ortho < 0 || o.mixed_ortho > 2 || o.inner_cycles < 0 || o.method < 0 || o.method > 1 ||
-        (o.method == 1 && o.mixed_precision) || o.precond < 0 || o.precond > DST_PRECOND_CN_SWEEP2 ||
+        (o.method == 1 && o.mixed_precision) || o.precond < 0 || o.precond > DST_PRECOND_CN_LEARNED ||
+        (o.precond == DST_PRECOND_CN_LEARNED && !dst_internal_unet_fits(mesh->unet, mesh)) ||
         (o.precond && (!o.mixed_precision || o.mixed_ortho != 2 || o.inner_cycles != 1 || o.method != 0))) {
         rc = DST_ERR_ARG;
     } else if (!mesh->d_psi0) {

@@ -59,6 +59,8 @@ struct OpParams {
     int tile_variant[2];     // apply tile shape per precision (index DST_FP64 / DST_FP32)
 };
 
+struct dst_unet;
+
 struct dst_mesh {
     int device;
     int d, nc;
@@ -84,7 +86,13 @@ struct dst_mesh {
     void *ws;
     size_t ws_bytes;
     double *host_pinned;          // page-locked host copy of the per-step records (lazily, by dst_solve)
+    dst_unet *unet;               // learned correction of the sweep preconditioner (not owned), or null
 };
+
+// The learned correction (unet.cu): z += s U(rho / s) with s = ||rho||; and
+// whether a network was built for this mesh's grid on its device.
+int dst_internal_unet_correct(dst_unet *u, const float2 *rho, float2 *z, cudaStream_t s);
+bool dst_internal_unet_fits(const dst_unet *u, const dst_mesh *mesh);
 
 // Testing hooks (dst_testing_set): the bulk-copy wait limit in force (the
 // standard one unless a test set another), and whether the next workspace

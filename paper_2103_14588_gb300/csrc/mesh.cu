@@ -98,7 +98,7 @@ OpParams dst_internal_params(const dst_mesh *mesh) {
     return p;
 }
 
-int dst_internal_tile_variants(const dst_mesh *mesh) { return mesh->d == 3 ? 1 : 3; }
+int dst_internal_tile_variants(const dst_mesh *mesh) { return mesh->d == 3 ? 2 : 3; }
 
 int dst_internal_tune(dst_mesh *mesh, void *scratch, cudaStream_t s) {
     const int nv = dst_internal_tile_variants(mesh);
@@ -249,6 +249,7 @@ extern "C" int dst_create_mesh(int d, const int64_t n_el[4], const double lo[4],
     m->d_V = nullptr;
     m->d_psi0 = nullptr;
     m->d_bd = nullptr;
+    m->unet = nullptr;
     m->ws = nullptr;
     m->host_pinned = nullptr;
     m->tile_variant[0] = m->tile_variant[1] = 0;

@@ -38,6 +38,7 @@
 
 #include "internal.h"
 #include "sweep.h"
+#include "fft.cuh"
 
 namespace {
 
@@ -124,134 +125,26 @@ __host__ __device__ inline void inv_small(cd (*A)[4], int n, cd (*R)[4]) {
 __host__ __device__ inline double mass_sym(double h, double th) { return h * (2.0 + cos(th)) / 3.0; }
 
 // ---- 1. time scan: s = S^-1 v -----------------------------------------------
+// The loads of the next PD layers are issued before a layer is combined.
 __global__ void time_scan_kernel(int64_t per, int64_t nt, const float2 *__restrict__ v, float2 *__restrict__ s) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= per) return;
+    constexpr int PD = 8;
+    float2 ring[PD];
+#pragma unroll
+    for (int q = 0; q < PD; ++q) ring[q] = nt - 1 - q >= 0 ? v[(nt - 1 - q) * per + e] : make_float2(0.f, 0.f);
     float2 acc = make_float2(0.f, 0.f);
-    for (int64_t t = nt - 1; t >= 0; --t) {
-        const float2 a = v[t * per + e];
-        acc = make_float2(2.f * a.x - acc.x, 2.f * a.y - acc.y);
-        s[t * per + e] = acc;
-    }
-}
-
-// ---- 2 / 4. FFT of planes over the periodic axes ------------------------------
-constexpr int FFT_THREADS = 256;
-constexpr int FFT_WARPS = FFT_THREADS / 32;
-
-// One line of length n (stride st in the plane) through the Stockham stages
-// `rad`, by one warp, with twiddles w[j] = exp(sign 2 pi i j / n) from the
-// table and two scratch lines a, b of n entries.
-__device__ void warp_fft_line(float2 *line, int st, int n, const int *rad, int nrad, const float2 *w, float2 *a,
-                              float2 *b) {
-    const int lane = threadIdx.x & 31;
-    for (int i = lane; i < n; i += 32) a[i] = line[i * st];
-    __syncwarp();
-    float2 *d0 = a, *d1 = b;
-    int Ns = 1;
-    for (int s = 0; s < nrad; ++s) {
-        const int R = rad[s];
-        const int q = n / R;               // butterflies of this stage
-        const int step = n / (Ns * R);     // twiddle index unit: exp(sign 2 pi i k / (Ns R)) = w[k * step]
-        for (int j = lane; j < q; j += 32) {
-            const int k = j % Ns;
-            const int dst = (j / Ns) * Ns * R + k;
-            if (R == 2) {
-                const float2 v0 = d0[j], v1 = cmulf(d0[j + q], w[k * step]);
-                d1[dst] = caddf(v0, v1);
-                d1[dst + Ns] = csubf(v0, v1);
-            } else if (R == 4) {
-                const float2 v0 = d0[j];
-                const float2 v1 = cmulf(d0[j + q], w[k * step]);
-                const float2 v2 = cmulf(d0[j + 2 * q], w[(2 * k * step) % n]);
-                const float2 v3 = cmulf(d0[j + 3 * q], w[(3 * k * step) % n]);
-                // omega = w[n/4] = exp(sign i pi/2) = sign * i
-                const float2 om = w[n / 4];
-                const float2 t0 = caddf(v0, v2), t1 = csubf(v0, v2);
-                const float2 t2 = caddf(v1, v3), t3 = cmulf(om, csubf(v1, v3));
-                d1[dst] = caddf(t0, t2);
-                d1[dst + Ns] = caddf(t1, t3);
-                d1[dst + 2 * Ns] = csubf(t0, t2);
-                d1[dst + 3 * Ns] = csubf(t1, t3);
-            } else {
-                // general radix: V_o = sum_r v_r exp(sign 2 pi i r o / R), v_r twiddled
-                for (int o = 0; o < R; ++o) {
-                    float2 acc = make_float2(0.f, 0.f);
-                    for (int r = 0; r < R; ++r) {
-                        const float2 vr = cmulf(d0[j + r * q], w[(int)(((long long)r * k * step) % n)]);
-                        acc = cfmaf(w[(int)(((long long)r * o * q) % n)], vr, acc);
-                    }
-                    d1[dst + o * Ns] = acc;
-                }
+    for (int64_t k0 = 0; k0 < nt; k0 += PD) {
+#pragma unroll
+        for (int q = 0; q < PD; ++q) {
+            const int64_t t = nt - 1 - (k0 + q);
+            if (t >= 0) {
+                const float2 a = ring[q];
+                if (t - PD >= 0) ring[q] = v[(t - PD) * per + e];
+                acc = make_float2(2.f * a.x - acc.x, 2.f * a.y - acc.y);
+                s[t * per + e] = acc;
             }
         }
-        __syncwarp();
-        float2 *t = d0; d0 = d1; d1 = t;
-        Ns *= R;
-    }
-    for (int i = lane; i < n; i += 32) line[i * st] = d0[i];
-    __syncwarp();
-}
-
-// One CTA per plane (batch b = layer, or layer x x-node in banded mode) and
-// component group: load into shared memory, FFT along the inner then the outer
-// axis, store.  Forward: node layout in, frequency layout [b][f][c] out;
-// inverse (sign +1): frequency layout in, node layout out, scaled by 1/(n1 n2).
-__global__ void __launch_bounds__(FFT_THREADS)
-fft_planes_kernel(SweepFft a, int inverse, const float2 *__restrict__ in, float2 *__restrict__ out) {
-    extern __shared__ __align__(16) float2 sm[];
-    const int n1 = a.n1, n2 = a.n2, nc = a.nc, ncb = a.ncb;
-    const int nf = n1 * n2;
-    float2 *plane = sm;                                   // [ncb][n1][n2]
-    float2 *w1 = plane + (size_t)ncb * nf;                // twiddles of the outer axis (n1)
-    float2 *w2 = w1 + n1;                                 // twiddles of the inner axis (n2)
-    float2 *scr = w2 + n2;                                // per warp two lines of nmax
-    const int nmax = n1 > n2 ? n1 : n2;
-    const int64_t b = blockIdx.x;
-    const int c0 = blockIdx.y * ncb;
-    const int64_t base = (b / a.nbx) * a.ns_nodes + (b % a.nbx);       // node index of (i1, i2) = (0, 0)
-    const float sign = inverse ? 1.f : -1.f;
-    for (int j = threadIdx.x; j < n1; j += FFT_THREADS) {
-        float sn, cs;
-        sincospif(2.f * (float)j / (float)n1, &sn, &cs);
-        w1[j] = make_float2(cs, sign * sn);
-    }
-    for (int j = threadIdx.x; j < n2; j += FFT_THREADS) {
-        float sn, cs;
-        sincospif(2.f * (float)j / (float)n2, &sn, &cs);
-        w2[j] = make_float2(cs, sign * sn);
-    }
-    // load
-    for (int idx = threadIdx.x; idx < nf * ncb; idx += FFT_THREADS) {
-        const int cc = idx % ncb, f = idx / ncb;
-        const int i1 = f / n2, i2 = f % n2;
-        float2 v;
-        if (inverse) v = in[(b * nf + f) * nc + c0 + cc];
-        else v = in[(base + (int64_t)i1 * a.s1 + (int64_t)i2 * a.s2) * nc + c0 + cc];
-        plane[(size_t)cc * nf + f] = v;
-    }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5;
-    float2 *sa = scr + (size_t)warp * 2 * nmax, *sb = sa + nmax;
-    if (n2 > 1)
-        for (int line = warp; line < ncb * n1; line += FFT_WARPS)
-            warp_fft_line(plane + (size_t)line * n2, 1, n2, a.rad2, a.nrad2, w2, sa, sb);
-    __syncthreads();
-    if (n1 > 1)
-        for (int line = warp; line < ncb * n2; line += FFT_WARPS) {
-            const int cc = line / n2, i2 = line % n2;
-            warp_fft_line(plane + (size_t)cc * nf + i2, n2, n1, a.rad1, a.nrad1, w1, sa, sb);
-        }
-    __syncthreads();
-    const float scale = inverse ? 1.f / (float)nf : 1.f;
-    for (int idx = threadIdx.x; idx < nf * ncb; idx += FFT_THREADS) {
-        const int cc = idx % ncb, f = idx / ncb;
-        const int i1 = f / n2, i2 = f % n2;
-        float2 v = plane[(size_t)cc * nf + f];
-        v.x *= scale;
-        v.y *= scale;
-        if (inverse) out[(base + (int64_t)i1 * a.s1 + (int64_t)i2 * a.s2) * nc + c0 + cc] = v;
-        else out[(b * nf + f) * nc + c0 + cc] = v;
     }
 }
 
@@ -301,24 +194,41 @@ __global__ void march_spectral_kernel(SweepGeom g, float2 *__restrict__ x) {
     float2 xp[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) xp[c] = make_float2(0.f, 0.f);
-    for (int64_t t = 0; t < g.nt; ++t) {
-        float2 *p = x + (t * nf + f) * NC;
-        float2 s[NC], xn[NC];
+    // the loads of the next PD layers are in flight while a layer is combined
+    constexpr int PD = 4;
+    float2 ring[PD][NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) s[c] = p[c];
+    for (int q = 0; q < PD; ++q)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            float2 acc = make_float2(0.f, 0.f);
+        for (int c = 0; c < NC; ++c)
+            ring[q][c] = q < g.nt ? x[((int64_t)q * nf + f) * NC + c] : make_float2(0.f, 0.f);
+    for (int64_t t0 = 0; t0 < g.nt; t0 += PD) {
 #pragma unroll
-            for (int d = 0; d < NC; ++d) {
-                acc = cfmaf(Pf[c][d], s[d], acc);
-                const float2 q = cmulf(Qf[c][d], xp[d]);
-                acc = csubf(acc, q);
+        for (int q = 0; q < PD; ++q) {
+            const int64_t t = t0 + q;
+            if (t < g.nt) {
+                float2 sv[NC], xn[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) sv[c] = ring[q][c];
+                if (t + PD < g.nt) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) ring[q][c] = x[((t + PD) * nf + f) * NC + c];
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int d = 0; d < NC; ++d) {
+                        acc = cfmaf(Pf[c][d], sv[d], acc);
+                        acc = csubf(acc, cmulf(Qf[c][d], xp[d]));
+                    }
+                    xn[c] = acc;
+                }
+                float2 *pt = x + (t * nf + f) * NC;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) { xp[c] = xn[c]; pt[c] = xn[c]; }
             }
-            xn[c] = acc;
         }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) { xp[c] = xn[c]; p[c] = xn[c]; }
     }
 }
 
@@ -421,70 +331,107 @@ __global__ void banded_factor_kernel(SweepGeom g, const double *__restrict__ Vx,
     }
 }
 
-// Row c of a structured block applied to the vector at node slot p of a team's
-// buffer (NC complex per node): a v_c + sum_k b_k phi_k(c) v_{pi_k(c)} + dc_c v_c.
+// FP32 coefficients of row c of the blocks (i, o) of Bd / Bl at one (y, z)
+// frequency, from the x-row entries xr = (M, C, W+, W-) and the frequency scalars
+// myz = my mz, sy mz, my sz:  a = i sgn M myz,  b_x = i (h_t/2) C myz,
+// b_y = -(h_t/2) M sy mz,  b_z = -(h_t/2) M my sz,  dc = -(h_t/2) W_beta(c) myz.
+struct FreqF {
+    float myz, symz, mysz, ht2;
+};
 template <int NC>
-__device__ __forceinline__ float2 blk_row(const float2 (&bk)[5], int c, const float2 *p, int nk) {
-    float2 acc = cmulf(bk[0], p[c]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-        if (k < nk) acc = cfmaf(bk[1 + k], p[spin_pi(NC, k, c)], acc);
-    return cfmaf(bk[4], p[c], acc);
-}
-// The coefficients of row c of a block in FP32: a, b_k phi_k(c), dc_c.
-template <int NC>
-__device__ __forceinline__ void blk_coefs(const Blk &B, int c, float2 (&bk)[5]) {
-    bk[0] = make_float2((float)B.a.x, (float)B.a.y);
-    for (int k = 0; k < 3; ++k) {
-        const cd v = B.b[k] * spin_phi(NC, k, c);
-        bk[1 + k] = make_float2((float)v.x, (float)v.y);
+__device__ __forceinline__ float2 row_apply(const float4 xr, const FreqF &q, float sgn, int c, int nk,
+                                            const float2 *p) {
+    const float M = xr.x, C = xr.y, Wc = (NC == 2 ? (c == 0) : (c < 2)) ? xr.z : xr.w;
+    // diagonal: (i sgn M myz - ht2 W myz) v_c
+    const float2 v = p[c];
+    const float ar = -q.ht2 * Wc * q.myz, ai = sgn * M * q.myz;
+    float2 acc = make_float2(ar * v.x - ai * v.y, ar * v.y + ai * v.x);
+    // alpha_x: i ht2 C myz phi_x(c) v_pi  (phi_x = 1)
+    {
+        const float2 u = p[NC == 2 ? 1 - c : 3 - c];
+        const float bi = q.ht2 * C * q.myz;
+        acc.x -= bi * u.y;
+        acc.y += bi * u.x;
     }
-    bk[4] = make_float2((float)B.dc[c], 0.f);
+    if (nk >= 2) {                       // alpha_y: -(ht2 M sy mz) phi_y(c) v_pi, phi_y = -i (even c), +i (odd c)
+        const float2 u = p[NC == 2 ? 1 - c : 3 - c];
+        const float br = -q.ht2 * M * q.symz;
+        if (c & 1) { acc.x -= br * u.y; acc.y += br * u.x; }
+        else { acc.x += br * u.y; acc.y -= br * u.x; }
+    }
+    if (nk >= 3) {                       // alpha_z: -(ht2 M my sz) phi_z(c) v_pi, phi_z = +1 (even c), -1 (odd c)
+        const float2 u = p[(c + 2) & 3];
+        const float br = -q.ht2 * M * q.mysz * ((c & 1) ? -1.f : 1.f);
+        acc.x += br * u.x;
+        acc.y += br * u.y;
+    }
+    return acc;
 }
 
-// NC lanes march one frequency; each team keeps its x-line (n nodes x NC) in
-// shared memory: the previous layer's solution, overwritten by the forward
-// elimination's y and then by this layer's solution.  Work layout [t][x][f][c].
+// NC lanes march one frequency.  Per team in shared memory: the x-line buffer
+// (the previous layer's solution, overwritten by the forward elimination's y and
+// then by this layer's solution) and the layer's right-hand side line; per CTA
+// the x-row entries of every node and offset.  Work layout [t][x][f][c].
 template <int NC>
 __global__ void march_banded_kernel(SweepGeom g, const double *__restrict__ Vx, const float2 *__restrict__ table,
                                     float2 *__restrict__ x) {
-    extern __shared__ __align__(16) float2 bufs[];
+    extern __shared__ __align__(16) float4 msm[];
     const int n = g.nx;
     const int64_t nf = (int64_t)g.n1 * g.n2;
+    const int teams = blockDim.x / NC;
     const int team = threadIdx.x / NC, c = threadIdx.x % NC;
-    const int64_t f = blockIdx.x * (int64_t)(blockDim.x / NC) + team;
+    const int64_t f = blockIdx.x * (int64_t)teams + team;
     const bool live = f < nf;
     const int64_t fl = live ? f : 0;
-    float2 *buf = bufs + (size_t)team * n * NC;
+    float4 *xr = msm;                                                    // [n][3]
+    float2 *buf = reinterpret_cast<float2 *>(xr + 3 * n) + (size_t)team * 2 * n * NC;
+    float2 *sln = buf + n * NC;
+    for (int k = threadIdx.x; k < 3 * n; k += blockDim.x) {
+        const XRow r = xrow(g, Vx, k / 3, k % 3 - 1);
+        xr[k] = make_float4((float)r.M, (float)r.C, (float)r.W[0], (float)r.W[1]);
+    }
     const unsigned lanebase = (threadIdx.x & 31) - c;
     double my, mz, sy, sz;
     yz_symbols(g, fl, my, mz, sy, sz);
+    FreqF q;
+    q.myz = (float)(my * mz);
+    q.symz = (float)(sy * mz);
+    q.mysz = (float)(my * sz);
+    q.ht2 = (float)(0.5 * g.ht);
     for (int i = c; i < n * NC; i += NC) buf[i] = make_float2(0.f, 0.f);
-    __syncwarp();
-    const float2 *tab = table + (size_t)fl * n * 2 * NC * NC;
+    __syncthreads();
+    const float2 *tab = table + (size_t)fl * n * 2 * NC * NC + c * NC;   // row c of L_i at tab + i * 2 NC^2
     for (int64_t t = 0; t < g.nt; ++t) {
-        float2 *xt = x + ((t * n) * nf + fl) * NC;         // node i at xt + i * nf * NC
+        float2 *xt = x + ((t * n) * nf + fl) * NC + c;                  // node i at xt + i * nf * NC
+        for (int i = 0; i < n; ++i) sln[i * NC + c] = live ? xt[(int64_t)i * nf * NC] : make_float2(0.f, 0.f);
+        __syncwarp();
+        // forward elimination, the factor rows of the next node loaded one node ahead
+        float2 Ln[NC];
+#pragma unroll
+        for (int d = 0; d < NC; ++d) Ln[d] = tab[d];
         float2 yprev = make_float2(0.f, 0.f);
         for (int i = 0; i < n; ++i) {
-            // r_i = s_t[i] - sum_o Bl(i, o) x_{t-1}[i + o]
-            float2 r = live ? xt[(int64_t)i * nf * NC + c] : make_float2(0.f, 0.f);
+            float2 Lc[NC];
+#pragma unroll
+            for (int d = 0; d < NC; ++d) Lc[d] = Ln[d];
+            if (i + 1 < n) {
+#pragma unroll
+                for (int d = 0; d < NC; ++d) Ln[d] = tab[(size_t)(i + 1) * 2 * NC * NC + d];
+            }
+            float2 r = sln[i * NC + c];
             if (t > 0) {
                 for (int o = -1; o <= 1; ++o) {
                     if (i + o < 0 || i + o >= n) continue;
-                    float2 bk[5];
-                    blk_coefs<NC>(xblock(g, xrow(g, Vx, i, o), NC, my, mz, sy, sz, -1.0), c, bk);
-                    r = csubf(r, blk_row<NC>(bk, c, buf + (i + o) * NC, g.d));
+                    r = csubf(r, row_apply<NC>(xr[3 * i + o + 1], q, -1.f, c, g.d, buf + (i + o) * NC));
                 }
             }
-            // y_i = r_i - L_i y_{i-1}
-            const float2 *Li = tab + (size_t)i * 2 * NC * NC + c * NC;
             float2 y = r;
 #pragma unroll
             for (int d = 0; d < NC; ++d) {
                 float2 yd;
                 yd.x = __shfl_sync(0xffffffffu, yprev.x, lanebase + d);
                 yd.y = __shfl_sync(0xffffffffu, yprev.y, lanebase + d);
-                y = csubf(y, cmulf(Li[d], yd));
+                y = csubf(y, cmulf(Lc[d], yd));
             }
             __syncwarp();                            // every lane has read x_{t-1}[i - 1]
             if (i > 0) buf[(i - 1) * NC + c] = yprev;
@@ -492,37 +439,37 @@ __global__ void march_banded_kernel(SweepGeom g, const double *__restrict__ Vx, 
         }
         buf[(n - 1) * NC + c] = yprev;
         __syncwarp();
-        // x_i = D_i^-1 (y_i - Bd(i, +1) x_{i+1})
+        // back substitution x_i = D_i^-1 (y_i - Bd(i, +1) x_{i+1}), factor rows one node ahead
+        float2 Dn[NC];
+#pragma unroll
+        for (int d = 0; d < NC; ++d) Dn[d] = tab[(size_t)(n - 1) * 2 * NC * NC + NC * NC + d];
         for (int i = n - 1; i >= 0; --i) {
-            float2 u = buf[i * NC + c];
-            if (i + 1 < n) {
-                float2 bk[5];
-                blk_coefs<NC>(xblock(g, xrow(g, Vx, i, 1), NC, my, mz, sy, sz, 1.0), c, bk);
-                u = csubf(u, blk_row<NC>(bk, c, buf + (i + 1) * NC, g.d));
+            float2 Dc[NC];
+#pragma unroll
+            for (int d = 0; d < NC; ++d) Dc[d] = Dn[d];
+            if (i > 0) {
+#pragma unroll
+                for (int d = 0; d < NC; ++d) Dn[d] = tab[(size_t)(i - 1) * 2 * NC * NC + NC * NC + d];
             }
-            const float2 *Di = tab + (size_t)i * 2 * NC * NC + NC * NC + c * NC;
+            float2 u = buf[i * NC + c];
+            if (i + 1 < n) u = csubf(u, row_apply<NC>(xr[3 * i + 2], q, 1.f, c, g.d, buf + (i + 1) * NC));
             float2 xi = make_float2(0.f, 0.f);
 #pragma unroll
             for (int d = 0; d < NC; ++d) {
                 float2 ud;
                 ud.x = __shfl_sync(0xffffffffu, u.x, lanebase + d);
                 ud.y = __shfl_sync(0xffffffffu, u.y, lanebase + d);
-                xi = cfmaf(Di[d], ud, xi);
+                xi = cfmaf(Dc[d], ud, xi);
             }
             __syncwarp();                            // every lane has read y_i and x_{i+1}
             buf[i * NC + c] = xi;
-            if (live) xt[(int64_t)i * nf * NC + c] = xi;
+            sln[i * NC + c] = xi;
             __syncwarp();
         }
+        if (live)
+            for (int i = 0; i < n; ++i) xt[(int64_t)i * nf * NC] = sln[i * NC + c];
+        __syncwarp();
     }
-}
-
-void radices(int n, int *r, int &nr) {
-    nr = 0;
-    while (n % 4 == 0) { r[nr++] = 4; n /= 4; }
-    while (n % 2 == 0) { r[nr++] = 2; n /= 2; }
-    for (int p = 3; n > 1; p += 2)
-        while (n % p == 0) { r[nr++] = p; n /= p; }
 }
 
 }  // namespace
@@ -577,6 +524,7 @@ int dst_sweep_plan(const dst_mesh *mesh, SweepPlan &p) {
     SweepFft &a = p.fft;
     a.nc = mesh->nc;
     a.nbx = banded ? (int)mesh->nu[0] : 1;
+    a.sbx = 1;
     a.ns_nodes = mesh->n_spatial;
     int64_t stride[3] = {1, mesh->nu[0], mesh->nu[0] * mesh->nu[1]};
     if (np == 1) {
@@ -597,8 +545,8 @@ int dst_sweep_plan(const dst_mesh *mesh, SweepPlan &p) {
     }
     a.n1 = g.n1;
     a.n2 = g.n2;
-    radices(a.n1, a.rad1, a.nrad1);
-    radices(a.n2, a.rad2, a.nrad2);
+    dst_fft::radices(a.n1, a.rad1, a.nrad1);
+    dst_fft::radices(a.n2, a.rad2, a.nrad2);
     p.banded = banded;
     p.has_fft = np > 0;
     p.nb = banded ? mesh->nt * mesh->nu[0] : mesh->nt;
@@ -608,28 +556,23 @@ int dst_sweep_plan(const dst_mesh *mesh, SweepPlan &p) {
         dst_internal_set_error_detail("Crank-Nicolson sweep: a periodic axis longer than 4096 nodes");
         return DST_ERR_ARG;
     }
-    const size_t fixed = sizeof(float2) * ((size_t)g.n1 + g.n2 + (size_t)FFT_WARPS * 2 * nmax);
     const size_t limit = 200 * 1024;
-    // components per FFT CTA: all of them when the plane fits and the planes alone fill the GPU
-    a.ncb = mesh->nc;
-    while (a.ncb > 1 && (fixed + sizeof(float2) * (size_t)a.ncb * nf > limit || p.nb * (mesh->nc / a.ncb) < 304))
-        a.ncb /= 2;
-    p.fft_smem = fixed + sizeof(float2) * (size_t)a.ncb * nf;
-    if (p.has_fft && p.fft_smem > limit) {
+    if (p.has_fft && !dst_fft::choose_layout<float2>(a, p.nb, limit)) {
         dst_internal_set_error_detail("Crank-Nicolson sweep: a periodic plane too large for shared memory");
         return DST_ERR_ARG;
     }
+    p.fft_smem = dst_fft::fft_smem_bytes<float2>(a);
     p.table_bytes = banded ? sizeof(float2) * (size_t)nf * g.nx * 2 * g.nc * g.nc : 0;
     // banded march: teams of NC lanes, shared memory of one x-line per team
     if (banded) {
-        const size_t line = sizeof(float2) * (size_t)g.nx * g.nc;
+        const size_t line = 2 * sizeof(float2) * (size_t)g.nx * g.nc;      // the x-line and the right-hand side line
         int teams = (int)((96 * 1024) / line);
         const int per_warp = 32 / g.nc;
         if (teams > 128 / g.nc) teams = 128 / g.nc;
         if (teams < per_warp) teams = per_warp;        // one warp at least (idle lanes if the line is long)
         teams = teams / per_warp * per_warp;
         p.march_threads = teams * g.nc;
-        p.march_smem = line * teams;
+        p.march_smem = line * teams + sizeof(float4) * 3 * (size_t)g.nx;
         if (p.march_smem > 200 * 1024) {
             dst_internal_set_error_detail("Crank-Nicolson sweep: x axis too long for the banded march");
             return DST_ERR_ARG;
@@ -681,7 +624,8 @@ int dst_sweep_apply(const SweepPlan &p, int64_t n_unknowns, const float2 *v, flo
     int dev = 0;
     DST_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !configured[dev]) {
-        DST_CUDA_TRY(cudaFuncSetAttribute(fft_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        DST_CUDA_TRY(cudaFuncSetAttribute(dst_fft::fft_planes_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          200 * 1024));
         DST_CUDA_TRY(cudaFuncSetAttribute(march_banded_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           200 * 1024));
         DST_CUDA_TRY(cudaFuncSetAttribute(march_banded_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -690,7 +634,7 @@ int dst_sweep_apply(const SweepPlan &p, int64_t n_unknowns, const float2 *v, flo
     }
     const dim3 fgrid((unsigned)p.nb, (unsigned)(p.g.nc / p.fft.ncb));
     if (p.has_fft) {
-        fft_planes_kernel<<<fgrid, FFT_THREADS, p.fft_smem, s>>>(p.fft, 0, z, work);
+        dst_fft::fft_planes_kernel<float2><<<fgrid, dst_fft::FFT_THREADS, p.fft_smem, s>>>(p.fft, 0, z, work);
         DST_CUDA_TRY(cudaGetLastError());
     }
     // 3. the march, in place on work
@@ -707,7 +651,7 @@ int dst_sweep_apply(const SweepPlan &p, int64_t n_unknowns, const float2 *v, flo
     DST_CUDA_TRY(cudaGetLastError());
     // 4. inverse FFT: work -> z (without an FFT the march ran on the node layout)
     if (p.has_fft) {
-        fft_planes_kernel<<<fgrid, FFT_THREADS, p.fft_smem, s>>>(p.fft, 1, work, z);
+        dst_fft::fft_planes_kernel<float2><<<fgrid, dst_fft::FFT_THREADS, p.fft_smem, s>>>(p.fft, 1, work, z);
         DST_CUDA_TRY(cudaGetLastError());
     } else {
         DST_CUDA_TRY(cudaMemcpyAsync(z, work, sizeof(float2) * n_unknowns, cudaMemcpyDeviceToDevice, s));

@@ -4,15 +4,17 @@
 #include "internal.h"
 
 // FFT of the planes of periodic axes: plane b covers the nodes
-// base(b) + i1 * s1 + i2 * s2 (i1 < n1, i2 < n2), base(b) = (b / nbx) * ns_nodes + b % nbx.
+// base(b) + i1 * s1 + i2 * s2 (i1 < n1, i2 < n2), base(b) = (b / nbx) * ns_nodes + (b % nbx) * sbx.
 struct SweepFft {
     int n1, n2;                 // outer and inner FFT lengths (1: no such axis)
     int64_t s1, s2;             // node strides of the two FFT dimensions
     int nbx;                    // batches per layer (x nodes in banded mode, else 1)
+    int64_t sbx;                // node stride between the batches of one layer
     int64_t ns_nodes;           // nodes of one layer
     int nc, ncb;                // spinor components, components per CTA
     int rad1[32], rad2[32];     // Stockham radices of each length
     int nrad1, nrad2;
+    int pingpong;               // 1: CTA-wide stages with a second plane buffer
 };
 
 struct SweepGeom {

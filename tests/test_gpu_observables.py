@@ -78,3 +78,62 @@ def test_zitterbewegung_2p1_full_size():
     assert np.abs(y_fem - y_ex).max() < 1e-3
     # the trembling is there: <x> rises and falls (not a monotone drift)
     assert x_ex.max() - x_ex[0] > 0.05 and np.any(np.diff(x_fem) < 0)
+
+
+# ---- energy per layer (dst_energy) ------------------------------------------------
+# FP64 FFTs (Stockham, O(log n) roundings per entry) against numpy's FFT in the
+# oracle: relative difference at rounding level, <= 1e-11 of the largest |E|.
+
+@pytest.mark.parametrize("d,n_el", [(1, [24, 1, 1, 5]), (1, [15, 1, 1, 3]), (2, [12, 10, 1, 4]), (2, [9, 14, 1, 3]),
+                                    (3, [6, 5, 4, 3]), (3, [8, 6, 10, 2])])
+def test_energy_parity(d, n_el):
+    import torch
+    from oracle import observables as OB
+    from paper_2103_14588_gb300 import binding as B
+    w = W.random_mesh(d, n_el, [P] * d, seed=d + 50, with_potential=False)
+    om = oracle_mesh(w)
+    rng = np.random.default_rng(d + 60)
+    psi = rng.standard_normal(om.unknown_shape) + 1j * rng.standard_normal(om.unknown_shape)
+    ref = OB.energy(om, psi, w.m)
+    with B.Mesh.from_workload(w) as mesh:
+        pd = torch.from_numpy(np.ascontiguousarray(psi).ravel()).cuda()
+        out = torch.full((om.nt,), float("nan"), dtype=torch.float64, device="cuda")
+        B.dst_energy(mesh.handle, pd, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 1e-11 * np.abs(ref).max()), (got, ref)
+
+
+def test_energy_of_the_plane_wave_solution():
+    """The 64 x 64 plane wave u_+(k) e^{ikx}: the FEM solution's energy per layer is the
+    exact E(k) x |u|^2 x length to the method's O(h^2) accuracy, and equals the oracle's."""
+    import torch
+    from oracle import observables as OB
+    from paper_2103_14588_gb300 import binding as B
+    w = W.plane_wave_1p1(n=64)
+    om = oracle_mesh(w)
+    with B.Mesh.from_workload(w) as mesh:
+        psi = torch.zeros(mesh.n_unknowns, dtype=torch.complex128, device="cuda")
+        st = B.dst_solve(mesh.handle, {"restart": 30, "rtol": 1e-12, "max_iters": 20000}, psi)
+        out = torch.zeros(om.nt, dtype=torch.float64, device="cuda")
+        B.dst_energy(mesh.handle, psi, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        x = psi.cpu().numpy().reshape(om.unknown_shape)
+    assert st["status"] == 0
+    ref = OB.energy(om, x, w.m)
+    assert np.all(np.abs(got - ref) <= 1e-11 * np.abs(ref).max())
+    E = np.sqrt(1.0 + 1.0)
+    assert np.all(np.abs(got / (E * 2 * np.pi) - 1.0) <= 2e-3)
+
+
+def test_energy_needs_periodic_axes():
+    import torch
+    from paper_2103_14588_gb300 import binding as B
+    w = W.random_mesh(2, [6, 5, 1, 3], [P, D], seed=1)
+    with B.Mesh.from_workload(w) as mesh:
+        psi = torch.zeros(mesh.n_unknowns, dtype=torch.complex128, device="cuda")
+        out = torch.zeros(3, dtype=torch.float64, device="cuda")
+        with pytest.raises(B.DstError) as e:
+            B.dst_energy(mesh.handle, psi, out)
+        assert e.value.code == B.DST_ERR_ARG
