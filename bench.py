@@ -56,8 +56,9 @@ FP64_FLOP_PER_CLK_SM = 4.0     # 2 FP64 FMA per clock per SM (1/64 of the FP32 r
 FP64_PROBE_TFLOPS = 1.196      # FP64 FMA throughput measured by a probe kernel on this machine
 CLASSES = ("apply64", "apply32", "cast", "project", "update", "scale", "misc", "rhs", "precond")
 # DRAM read+write bytes per algorithmic byte of a kernel class, from one ncu capture of
-# its kernel as committed (profiles/*.md); None: no capture of the current kernel.
-TRAFFIC_RATIO = {}
+# its kernel as committed (profiles/gram_schmidt_klein_3p1_32.md: update_f32_kernel at
+# 4.06M unknowns, nv = 11); classes without a capture of the current kernel are absent.
+TRAFFIC_RATIO = {"update": 0.987}
 
 
 def measured_peaks():
@@ -300,33 +301,62 @@ def time_apply(torch, B, mesh, prec, n, iters=40):
     return ms, 2.0 * n * esz / (ms * 1e-3) / 1e9
 
 
-NCU_CASES = ("solve60", "solve60_klein32", "apply32_zb", "apply32_klein", "apply64_klein")
+NCU_CASES = ("solve60", "solve60_klein32", "solve60_klein", "apply32_zb", "apply32_klein", "apply64_klein",
+             "apply32_klein_zcol", "apply64_klein_zcol", "sweep_zb", "unet_zb48")
 
 
 def run_ncu_case(case):
     """Small fixed launches for ncu captures (nothing timed, nothing printed as a bench line).
 
-    solve60: the first 60 Arnoldi steps (two GMRES(30) cycles) of the bench's mixed solve;
-    solve60_klein32: the same on the 3+1 Klein workload at 32^3 x 32 (4.06M unknowns, large
-    enough for the bulk-copy fed projection);
-    apply32_zb / apply32_klein / apply64_klein: 12 operator applies on the 96^2 x 96 bench
-    mesh or the 48^3 x 48 3+1 Klein mesh, over rotating buffers.
+    solve60: the first 60 Arnoldi steps (two GMRES(30) cycles) of the 2+1 mixed solve
+    (96^2 x 96); solve60_klein32 / solve60_klein: the same on the 3+1 Klein workload at
+    32^3 x 32 (4.06M unknowns) or 48^3 x 48 (the bench mesh, seed 1), with the bench's
+    one-pass Gram-Schmidt;
+    apply32_zb / apply32_klein / apply64_klein: 12 operator applies on the 96^2 x 96 mesh or
+    the 48^3 x 48 3+1 Klein mesh, over rotating buffers (tile variant 0);
+    apply32_klein_zcol / apply64_klein_zcol: the same with the z-column kernel (variant 1);
+    sweep_zb: 6 Crank-Nicolson sweeps on the 96^2 x 96 mesh;
+    unet_zb48: 4 forward passes of the U-Net on the 48^2 x 48 grid.
     """
     import torch
     from paper_2103_14588_gb300 import binding as B
     torch.cuda.set_device(0)
     if case == "solve60_klein32":
         w = W.klein_3p1(n=32, nt=32, p0=1.05)
+    elif case == "solve60_klein":
+        w = W.klein_3p1(seed=1)
+    elif case == "unet_zb48":
+        w = W.zb_2p1(n=48, nt=48)
     else:
-        w = W.klein_3p1(p0=1.05) if case.endswith("klein") else W.zb_2p1()
+        w = W.klein_3p1(p0=1.05) if "klein" in case else W.zb_2p1()
     with B.Mesh.from_workload(w) as m:
         if case.startswith("solve60"):
             psi = torch.zeros(m.n_unknowns, dtype=torch.complex128, device="cuda")
-            st = B.dst_solve(m.handle, {"restart": RESTART, "rtol": RTOL, "max_iters": 60, "mixed_precision": 1}, psi)
+            st = B.dst_solve(m.handle, {"restart": RESTART, "rtol": RTOL, "max_iters": 60, "mixed_precision": 1,
+                                        "ortho": ORTHO}, psi)
             torch.cuda.synchronize()
             print("solve60: %d steps, status %d, %d second passes" % (st["iters"], st["status"], st["reorths"]))
+        elif case == "sweep_zb":
+            v = torch.randn(m.n_unknowns, dtype=torch.complex64, device="cuda")
+            z = torch.empty_like(v)
+            for _ in range(6):
+                B.dst_precond_apply(m.handle, B.DST_PRECOND_CN_SWEEP, v, z)
+            torch.cuda.synchronize()
+            print("sweep_zb: 6 sweeps")
+        elif case == "unet_zb48":
+            net = B.UNet(m.handle)
+            net.set_params(np.random.default_rng(1).standard_normal(net.num_params).astype(np.float32) * 0.05)
+            v = torch.randn(m.n_unknowns, dtype=torch.complex64, device="cuda")
+            z = torch.empty_like(v)
+            for _ in range(4):
+                net.forward(v, z)
+            torch.cuda.synchronize()
+            net.close()
+            print("unet_zb48: 4 forward passes")
         else:
             prec = B.DST_FP32 if case.startswith("apply32") else B.DST_FP64
+            if case.endswith("_zcol"):
+                B.dst_set_apply_variant(m.handle, prec, 1)
             ms, gbs = time_apply(torch, B, m.handle, prec, m.n_unknowns, iters=12)
             print("%s: %.1f us per apply" % (case, 1e3 * ms))
 
@@ -415,6 +445,32 @@ def apply_figures(torch, B, mesh_obj, st_prof, hbm):
     return out
 
 
+def run_batch_stated(torch, B, count, cap=4000):
+    """A sample of the batched workload at its stated shape: every axis (time included) drawn
+    from 32..256 for 1+1 and 2+1 alike (workloads.batch_instances with the full ranges), solved
+    by one dst_solve_batch call with a cap of `cap` Arnoldi steps per instance; converged and
+    capped instances are reported separately."""
+    ws = W.batch_instances(count, 4, n1=(32, 256), n2=(32, 256))
+    meshes = [B.Mesh.from_workload(w) for w in ws]
+    psis = [torch.zeros(m.n_unknowns, dtype=torch.complex128, device="cuda") for m in meshes]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, sts = B.dst_solve_batch([m.handle for m in meshes], {"rtol": RTOL, "max_iters": cap, "max_refine": 100000},
+                                psis)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    conv = [i for i, st in enumerate(sts) if st["status"] == 0]
+    out = {"instances": count, "cap_arnoldi_steps": cap, "wall_s": tb,
+           "unknowns": [int(m.n_unknowns) for m in meshes], "dims": [w.d for w in ws],
+           "converged": len(conv), "capped": count - len(conv),
+           "converged_solves_per_s": len(conv) / tb,
+           "converged_unknowns": int(sum(meshes[i].n_unknowns for i in conv)),
+           "arnoldi_steps": int(sum(st["iters"] for st in sts))}
+    for m in meshes:
+        m.close()
+    return out
+
+
 def run_precond_bench(torch, B):
     """Flexible GMRES with the Crank-Nicolson sweep, and with the sweep plus the learned
     U-Net correction (trained here on pairs generated on the GPU), against the plain
@@ -441,10 +497,11 @@ def run_precond_bench(torch, B):
                 params[-(2 * m.ncomp * 16 + 2 * m.ncomp):] = 0.0
                 net.set_params(params)
                 t0 = time.perf_counter()
-                losses = net.train(m.handle, steps=300, lr=5e-4, seed=17)
-                rec["training"] = {"steps": 300, "seconds": time.perf_counter() - t0,
+                losses = net.train(m.handle, steps=600, lr=5e-4, seed=17)
+                rec["training"] = {"steps": 600, "seconds": time.perf_counter() - t0,
                                    "loss_first_20": float(_np.mean(losses[:20])),
-                                   "loss_last_20": float(_np.mean(losses[-20:]))}
+                                   "loss_last_20": float(_np.mean(losses[-20:])),
+                                   "output_scale": net.output_scale()}
                 B.dst_set_learned_precond(m.handle, net)
                 runs.append(("cn_sweep_learned", dict(base, precond=B.DST_PRECOND_CN_LEARNED)))
             for name, o in runs:
@@ -468,6 +525,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve throughput cases")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned-solve comparison")
+    ap.add_argument("--batch-stated", type=int, default=0,
+                    help="only solve this many batched instances drawn at the stated 32..256 shape and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed solves (no FP64 comparisons, second workload, applies)")
     ap.add_argument("--ncu-case", choices=NCU_CASES, help="run one small case for an ncu capture and exit")
@@ -481,6 +540,12 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.batch_stated:
+        import torch
+        from paper_2103_14588_gb300 import binding as B
+        torch.cuda.set_device(local)
+        print(json.dumps({"batch_stated_shape": run_batch_stated(torch, B, args.batch_stated)}))
         return
 
     import torch

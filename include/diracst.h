@@ -454,8 +454,8 @@ DST_API int dst_energy(const dst_mesh *mesh, const void *psi, void *out, void *s
  * dst_unet_create: a network for the mesh's grid, parameters zero; DEVICE
  *   memory for parameters, Adam moments, activations and their gradients.
  * dst_unet_num_params / set_params / get_params: the flat FP32 vector (HOST).
- * dst_unet_forward: y = ||x|| U(x / ||x||), x and y DEVICE FP32 complex vectors
- *   of the mesh's n_unknowns entries (distinct).
+ * dst_unet_forward: y = gamma ||x|| U(x / ||x||), x and y DEVICE FP32 complex
+ *   vectors of the mesh's n_unknowns entries (distinct).
  * dst_unet_loss_grad: for DEVICE x, target: L = ||U(x^) - t^||^2 / ||t^||^2 with
  *   x^ = x / ||x||, t^ = target / ||x||; *loss (HOST) and the gradient of L with
  *   respect to every parameter (HOST, num_params floats; either may be NULL).
@@ -463,8 +463,12 @@ DST_API int dst_energy(const dst_mesh *mesh, const void *psi, void *out, void *s
  * dst_unet_train: `steps` Adam steps (learning rate lr, beta 0.9 / 0.999) on
  *   pairs the method generates on the GPU: e standard normal (splitmix64 of
  *   seed and index), r = A e, z = M_CN(r), input rho = r - A z, target e - z;
- *   loss per step into loss_host (HOST, `steps` floats, may be NULL).  The mesh
- *   must be one the sweep covers.  Synchronises the stream.
+ *   loss per step into loss_host (HOST, `steps` floats, may be NULL).  Then the
+ *   output scale gamma of the correction, z += gamma s U(rho / s), is set to the
+ *   least-squares factor <U, t> / ||U||^2 over 8 fresh pairs (0 if negative), so
+ *   that on such pairs the scaled correction never leaves a larger error than
+ *   the sweep alone.  The mesh must be one the sweep covers.  Synchronises.
+ * dst_unet_output_scale: the current gamma (1 after create / set_params).
  * dst_set_learned_precond: use `net` (NULL: none) in solves of this mesh with
  *   precond = DST_PRECOND_CN_LEARNED.  The mesh does not own it; solves that
  *   share one network must not overlap.
@@ -482,6 +486,7 @@ DST_API int dst_unet_loss_grad(dst_unet *net, const void *x, const void *target,
                                void *stream);
 DST_API int dst_unet_train(dst_unet *net, dst_mesh *mesh, int steps, float lr, uint64_t seed, float *loss,
                            void *stream);
+DST_API int dst_unet_output_scale(const dst_unet *net, double *gamma);
 DST_API int dst_set_learned_precond(dst_mesh *mesh, dst_unet *net);
 
 /* Static, human-readable name of a status code. */

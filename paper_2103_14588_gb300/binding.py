@@ -32,7 +32,7 @@ EXPORTED = (
     "dst_set_boundary_data", "dst_precond_apply", "dst_energy",
     "dst_unet_create", "dst_unet_destroy", "dst_unet_num_params", "dst_unet_set_params", "dst_unet_get_params",
     "dst_unet_forward", "dst_unet_loss_grad", "dst_unet_train", "dst_set_learned_precond",
-    "dst_testing_fp32_arnoldi",
+    "dst_testing_fp32_arnoldi", "dst_unet_output_scale",
 )
 
 
@@ -114,6 +114,7 @@ def _load():
         "dst_unet_loss_grad": (c_int, [vp, vp, vp, P(c_double), vp, vp]),
         "dst_unet_train": (c_int, [vp, vp, c_int, ctypes.c_float, ctypes.c_uint64, vp, vp]),
         "dst_set_learned_precond": (c_int, [vp, vp]),
+        "dst_unet_output_scale": (c_int, [vp, P(c_double)]),
         "dst_testing_fp32_arnoldi": (c_int, [c_int, i64, c_int, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -428,6 +429,11 @@ class UNet:
                                    losses.ctypes.data, stream if isinstance(stream, int) else stream.cuda_stream),
                "dst_unet_train")
         return losses[:steps]
+
+    def output_scale(self):
+        g = ctypes.c_double()
+        _check(_lib.dst_unet_output_scale(self.handle, ctypes.byref(g)), "dst_unet_output_scale")
+        return g.value
 
     def close(self):
         if self.handle:

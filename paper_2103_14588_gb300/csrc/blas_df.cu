@@ -377,16 +377,18 @@ project_f32_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
 // independent of the arithmetic, in contiguous 16 KB transfers, refilling a
 // slot once all eight consumer warps have released it.  Each CTA owns a
 // contiguous slice of entries, cut into 2048-entry chunks; the copy sequence
-// is, per group of four basis vectors and per chunk, the chunk of w and then
+// is, per group of TMA_GROUP basis vectors and per chunk, the chunk of w and then
 // the chunks of the group's vectors (w is read once per group: reducing every
 // vector's chunk contribution over the warp instead, to read w once, made the
-// consumers the bottleneck).  Each chunk's contribution is accumulated in the
+// consumers the bottleneck; groups of eight read w a quarter as often as groups
+// of four for nvec = 30).  Each chunk's contribution is accumulated in the
 // anchored scheme with a bound taken from that chunk of w, then folded into a
 // df32 per-thread sum.
 constexpr int TMA_CHUNK = 2048;                 // entries per copy (16 KB)
 constexpr int TMA_SLOTS = 6;                    // ring: 6 x 16 KB (two CTAs per SM)
 constexpr int TMA_SMEM = TMA_SLOTS * TMA_CHUNK * 8;
 constexpr unsigned TMA_WAIT_LIMIT = 1u << 22;   // try_wait attempts before a wait is declared failed
+constexpr int TMA_GROUP = 8;                    // basis vectors per pass over a chunk of w
 
 constexpr int TMA_THREADS = DF_THREADS + 32;   // eight consumer warps and one producer warp
 
@@ -423,7 +425,7 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
     df_slice2(n, b, e);
     const int64_t len = e > b ? e - b : 0;
     const int nch = (int)((len + TMA_CHUNK - 1) / TMA_CHUNK);
-    const int ngr = (nvec + 3) / 4;
+    const int ngr = (nvec + TMA_GROUP - 1) / TMA_GROUP;
     const int K = nch * (ngr + nvec);                // copies this CTA consumes
     if (tid == 0) {
         for (int q = 0; q < TMA_SLOTS; ++q) {
@@ -450,10 +452,10 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
                     *vfailed = 1;
                     break;
                 }
-                const int gv = nvec - 4 * pg < 4 ? nvec - 4 * pg : 4;
+                const int gv = nvec - TMA_GROUP * pg < TMA_GROUP ? nvec - TMA_GROUP * pg : TMA_GROUP;
                 const int64_t c0 = b + (int64_t)pc * TMA_CHUNK;
                 const int64_t cnt = e - c0 < TMA_CHUNK ? e - c0 : TMA_CHUNK;
-                const float2 *src = pq == 0 ? w + c0 : V + (int64_t)(4 * pg + pq - 1) * n + c0;
+                const float2 *src = pq == 0 ? w + c0 : V + (int64_t)(TMA_GROUP * pg + pq - 1) * n + c0;
                 const unsigned bytes = (unsigned)(cnt * (int64_t)sizeof(float2));
                 mbar_arrive_expect_tx(&full[slot], bytes);
                 bulk_g2s(ring + (size_t)slot * U, src, bytes, &full[slot]);
@@ -485,10 +487,10 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
         };
         bool stop = false;
         for (int g = 0; g < ngr && !stop; ++g) {
-            const int gv = nvec - 4 * g < 4 ? nvec - 4 * g : 4;
-            DfAcc R[4], I[4];
+            const int gv = nvec - TMA_GROUP * g < TMA_GROUP ? nvec - TMA_GROUP * g : TMA_GROUP;
+            DfAcc R[TMA_GROUP], I[TMA_GROUP];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { R[q].zero(); I[q].zero(); }
+            for (int q = 0; q < TMA_GROUP; ++q) { R[q].zero(); I[q].zero(); }
             for (int c = 0; c < nch && !stop; ++c) {
                 const int64_t c0 = b + (int64_t)c * TMA_CHUNK;
                 const int units = (int)(((e - c0 < TMA_CHUNK) ? e - c0 : TMA_CHUNK) >> 1);
@@ -535,10 +537,13 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
             }
             if (stop) break;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < TMA_GROUP; ++q) {
                 if (q < gv) {
                     const double sr = dfwarp_sum(R[q]), si = dfwarp_sum(I[q]);
-                    if (lane == 0) { red[warp][2 * (4 * g + q)] = sr; red[warp][2 * (4 * g + q) + 1] = si; }
+                    if (lane == 0) {
+                        red[warp][2 * (TMA_GROUP * g + q)] = sr;
+                        red[warp][2 * (TMA_GROUP * g + q) + 1] = si;
+                    }
                 }
             }
         }

@@ -226,11 +226,31 @@ __global__ void loss_kernel(int64_t n, const float *__restrict__ y, const float 
     if (threadIdx.x == 0) *loss = red[0] / tn;
 }
 
-// z += s y (the network's output scaled back; y [N][C] is the same floats as a complex vector)
-__global__ void axpy_scaled_kernel(int64_t n, const float *__restrict__ s, const float *__restrict__ y,
-                                   float *__restrict__ z) {
+// z += g s y (the network's output scaled back; y [N][C] is the same floats as a complex vector)
+__global__ void axpy_scaled_kernel(int64_t n, const float *__restrict__ s, const float *__restrict__ g,
+                                   const float *__restrict__ y, float *__restrict__ z) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) z[i] += *s * y[i];
+    if (i < n) z[i] += *g * *s * y[i];
+}
+
+// <y, t / s> and ||y||^2 accumulated into acc[0], acc[1] (one CTA, FP64)
+__global__ void dot_kernel(int64_t n, const float *__restrict__ y, const float *__restrict__ t,
+                           const float *__restrict__ s, double *__restrict__ acc) {
+    __shared__ double r1[256], r2[256];
+    const float inv = 1.0f / *s;
+    double a = 0.0, b = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        a += (double)y[i] * (double)(t[i] * inv);
+        b += (double)y[i] * (double)y[i];
+    }
+    r1[threadIdx.x] = a;
+    r2[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) { r1[threadIdx.x] += r1[threadIdx.x + w]; r2[threadIdx.x] += r2[threadIdx.x + w]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { acc[0] += r1[0]; acc[1] += r2[0]; }
 }
 
 // standard normal pairs from splitmix64 of (seed, index) by Box-Muller
@@ -270,6 +290,8 @@ struct dst_unet {
     float *x0, *a1, *s1, *p1, *a2, *s2, *p2, *a3, *h3, *u2, *q2, *r2, *u1, *q1, *r1, *y;
     float *g_big1, *g_big2, *g_big3, *gs1, *gs2, *g_mid;   // gradient scratch
     float *scale;                                          // device scalar s
+    float *gamma;                                          // device scalar: output scale of the correction
+    double gamma_host;
     double *dscr;                                          // device doubles: [0] sum sq, [1] loss, [2] target sumsq
     int64_t act_floats;
     void *mem;
@@ -377,13 +399,17 @@ static int unet_create(const dst_mesh *mesh, dst_unet **out) {
     u->gs2 = (float *)(b + o_gs2);
     u->g_mid = (float *)(b + o_gm);
     u->scale = (float *)(b + o_sc);
+    u->gamma = u->scale + 1;
     u->dscr = (double *)(b + o_ds);
     cudaError_t e = cudaMemset(u->mem, 0, total);
+    const float one = 1.0f;
+    if (e == cudaSuccess) e = cudaMemcpy(u->gamma, &one, sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(u->mem);
         delete u;
         DST_CUDA_TRY(e);
     }
+    u->gamma_host = 1.0;
     *out = u;
     return DST_OK;
 }
@@ -559,7 +585,7 @@ int dst_internal_unet_correct(dst_unet *u, const float2 *rho, float2 *z, cudaStr
     int rc;
     if ((rc = norm_into_scale(u, x, n, s))) return rc;
     if ((rc = forward(u, x, u->scale, s))) return rc;
-    axpy_scaled_kernel<<<nblk(n), 256, 0, s>>>(n, u->scale, u->y, reinterpret_cast<float *>(z));
+    axpy_scaled_kernel<<<nblk(n), 256, 0, s>>>(n, u->scale, u->gamma, u->y, reinterpret_cast<float *>(z));
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
@@ -594,6 +620,9 @@ extern "C" int dst_unet_set_params(dst_unet *u, const float *host) {
     if (!u || !host) return DST_ERR_ARG;
     DST_CUDA_TRY(cudaMemcpy(u->params, host, sizeof(float) * u->nparams, cudaMemcpyHostToDevice));
     DST_CUDA_TRY(cudaMemset(u->adam_m, 0, 2 * sizeof(float) * u->nparams));
+    const float one = 1.0f;
+    DST_CUDA_TRY(cudaMemcpy(u->gamma, &one, sizeof(float), cudaMemcpyHostToDevice));
+    u->gamma_host = 1.0;
     u->packed = false;
     return DST_OK;
 }
@@ -612,7 +641,7 @@ extern "C" int dst_unet_forward(dst_unet *u, const void *x, void *y, void *strea
     if (rc == DST_OK) rc = forward(u, (const float *)x, u->scale, s);
     if (rc) return rc;
     DST_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(float) * n, s));
-    axpy_scaled_kernel<<<nblk(n), 256, 0, s>>>(n, u->scale, u->y, (float *)y);
+    axpy_scaled_kernel<<<nblk(n), 256, 0, s>>>(n, u->scale, u->gamma, u->y, (float *)y);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
@@ -674,6 +703,38 @@ static int train(dst_unet *u, dst_mesh *mesh, int steps, float lr, uint64_t seed
                                                       c1, c2, 1e-8f);
         if ((rc = pack(u, s))) break;
     }
+    // output scale: the least-squares factor gamma = <U, t> / ||U||^2 over fresh pairs, so
+    // that the scaled correction's error on them is never above the sweep's own
+    if (rc == DST_OK && steps > 0) {
+        const int nval = 8;
+        double *acc = u->dscr + 2;                      // [2], [3]; dscr[2] is reused by loss_grad only
+        if (cudaMemsetAsync(acc, 0, 2 * sizeof(double), s) != cudaSuccess) rc = DST_ERR_CUDA;
+        for (int it = 0; it < nval && rc == DST_OK; ++it) {
+            randn_kernel<<<nblk(n), 256, 0, s>>>(n, ~seed + (uint64_t)it * 0xD1B54A32D192ED03ull, e);
+            if ((rc = dst_internal_apply(mesh, DST_FP32, e, r, s))) break;
+            if ((rc = dst_sweep_apply(plan, n, r, z, s))) break;
+            if ((rc = dst_internal_apply(mesh, DST_FP32, z, az, s))) break;
+            if ((rc = dst_k_sub_f32(n, r, az, r, s))) break;
+            if ((rc = dst_k_sub_f32(n, e, z, tg, s))) break;
+            const float *x = (const float *)r;
+            if ((rc = norm_into_scale(u, x, 2 * n, s))) break;
+            if ((rc = forward(u, x, u->scale, s))) break;
+            dot_kernel<<<1, 256, 0, s>>>(2 * n, u->y, (const float *)tg, u->scale, acc);
+        }
+        double hacc[2] = {0.0, 0.0};
+        if (rc == DST_OK && (cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                             cudaStreamSynchronize(s) != cudaSuccess))
+            rc = DST_ERR_CUDA;
+        if (rc == DST_OK) {
+            double gmm = hacc[1] > 0.0 ? hacc[0] / hacc[1] : 0.0;
+            if (!(gmm > 0.0)) gmm = 0.0;
+            const float gf = (float)gmm;
+            u->gamma_host = gmm;
+            if (cudaMemcpyAsync(u->gamma, &gf, sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                rc = DST_ERR_CUDA;
+        }
+    }
     if (rc == DST_OK && steps > 0 && loss_host) {
         if (cudaMemcpyAsync(losses.data(), lossd, sizeof(double) * steps, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
@@ -690,6 +751,12 @@ extern "C" int dst_unet_train(dst_unet *u, dst_mesh *mesh, int steps, float lr, 
                               void *stream) {
     if (!u || !mesh || steps < 0 || !(lr > 0)) return DST_ERR_ARG;
     return dst_internal_guard("dst_unet_train", [&] { return train(u, mesh, steps, lr, seed, loss_host, (cudaStream_t)stream); });
+}
+
+extern "C" int dst_unet_output_scale(const dst_unet *u, double *gamma) {
+    if (!u || !gamma) return DST_ERR_ARG;
+    *gamma = u->gamma_host;
+    return DST_OK;
 }
 
 extern "C" int dst_set_learned_precond(dst_mesh *mesh, dst_unet *u) {

@@ -129,6 +129,8 @@ def test_training_lowers_the_loss_and_the_correction_solves():
         assert np.all(np.isfinite(losses))
         assert abs(losses[0] - 1.0) < 1e-3
         assert losses[-50:].mean() < 0.98, (losses[:50].mean(), losses[-50:].mean())
+        gamma = net.output_scale()
+        assert 0.0 <= gamma <= 2.0, gamma
         B.dst_set_learned_precond(mesh.handle, net)
         psi = torch.zeros(mesh.n_unknowns, dtype=torch.complex128, device="cuda")
         base = {"restart": 30, "rtol": 1e-9, "max_iters": 5000, "mixed_precision": 1}
@@ -138,8 +140,8 @@ def test_training_lowers_the_loss_and_the_correction_solves():
         ss = B.dst_solve(mesh.handle, dict(base, precond=B.DST_PRECOND_CN_SWEEP), psi)
         B.dst_set_learned_precond(mesh.handle, None)
         net.close()
-    print("steps with the trained correction %d, sweep alone %d; loss %.3f -> %.3f"
-          % (sl["iters"], ss["iters"], losses[:50].mean(), losses[-50:].mean()))
+    print("steps with the trained correction %d, sweep alone %d; loss %.3f -> %.3f, output scale %.3f"
+          % (sl["iters"], ss["iters"], losses[:50].mean(), losses[-50:].mean(), gamma))
     assert sl["status"] == 0 and rel_l2(x, ref) <= 1e-8
     assert ss["status"] == 0
     assert sl["iters"] <= 1.5 * ss["iters"] + 10, (sl["iters"], ss["iters"])
