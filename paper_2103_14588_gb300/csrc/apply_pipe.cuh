@@ -195,18 +195,22 @@ __device__ __forceinline__ void add_i_alpha(int k, T s, const V *P, V *G) {
 }
 
 // G_C' and G_M' of a node whose stencils are the standard interior ones.
-// WV: x-only potential weights (w = m beta + V per x element) instead of m beta.
+// WV: x-only potential.  The mass-plus-potential x stencil of a node between
+// elements of weights w_l, w_r (w = m beta + V) is (w_l, 2 (w_l + w_r), w_r)
+// = (w_l + w_r)/2 [1,4,1] + (w_r - w_l)/2 [-1,0,1], so G_M' = a QM + b QCx with
+// a = -km (w_l + w_r) / 2 and b = -km (w_r - w_l) / 2: both fields are needed
+// anyway, and b = 0 away from a jump of V.
 template <int D, int NC, typename T, bool WV, typename Get>
-__device__ __forceinline__ void fields_std(Get get, const StdConst<T> &sc, T m, const T (&wx)[2][3],
+__device__ __forceinline__ void fields_std(Get get, const StdConst<T> &sc, T m, const T (&wa)[2], const T (&wb)[2],
                                            typename C2<T>::type *GC, typename C2<T>::type *GM) {
     using V = typename C2<T>::type;
     const int NZ = D >= 3 ? 3 : 1, NY = D >= 2 ? 3 : 1;
-    V QM[NC], QCx[NC], QCy[NC], QCz[NC], QW[NC];   // sums over z of [1,4,1] (and [-1,0,1] for z)
+    V QM[NC], QCx[NC], QCy[NC], QCz[NC];   // sums over z of [1,4,1] (and [-1,0,1] for z)
 #pragma unroll
-    for (int c = 0; c < NC; ++c) { QM[c] = cz<V>(); QCx[c] = cz<V>(); QCy[c] = cz<V>(); QCz[c] = cz<V>(); QW[c] = cz<V>(); }
+    for (int c = 0; c < NC; ++c) { QM[c] = cz<V>(); QCx[c] = cz<V>(); QCy[c] = cz<V>(); QCz[c] = cz<V>(); }
 #pragma unroll
     for (int dz = 0; dz < NZ; ++dz) {
-        V PM[NC], PCx[NC], PCy[NC], PW[NC];
+        V PM[NC], PCx[NC], PCy[NC];
 #pragma unroll
         for (int dy = 0; dy < NY; ++dy) {
             const int r = (dz * NY + dy) * 3;
@@ -215,20 +219,15 @@ __device__ __forceinline__ void fields_std(Get get, const StdConst<T> &sc, T m, 
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const V x0 = n0.c[c], x1 = n1.c[c], x2 = n2.c[c];
-                V rM, rC, rW;
+                V rM, rC;
                 rM.x = fma((T)4, x1.x, x0.x + x2.x); rM.y = fma((T)4, x1.y, x0.y + x2.y);
                 rC.x = x2.x - x0.x; rC.y = x2.y - x0.y;
-                if (WV) {
-                    const int sb = Beta<D>::s(c) > 0 ? 0 : 1;
-                    rW = cfma_r(wx[sb][0], x0, cfma_r(wx[sb][1], x1, cmul_r(wx[sb][2], x2)));
-                }
                 if (dy == 0) {
-                    PM[c] = rM; PCx[c] = rC; if (WV) PW[c] = rW;
+                    PM[c] = rM; PCx[c] = rC;
                     if (D >= 2) { PCy[c].x = -rM.x; PCy[c].y = -rM.y; }
                 } else {
                     PM[c] = cfma_r(wy, rM, PM[c]);
                     PCx[c] = cfma_r(wy, rC, PCx[c]);
-                    if (WV) PW[c] = cfma_r(wy, rW, PW[c]);
                     if (D >= 2 && dy == 2) PCy[c] = cadd(PCy[c], rM);
                 }
             }
@@ -238,7 +237,6 @@ __device__ __forceinline__ void fields_std(Get get, const StdConst<T> &sc, T m, 
         for (int c = 0; c < NC; ++c) {
             QM[c] = cfma_r(wz, PM[c], QM[c]);
             QCx[c] = cfma_r(wz, PCx[c], QCx[c]);
-            if (WV) QW[c] = cfma_r(wz, PW[c], QW[c]);
             if (D >= 2) QCy[c] = cfma_r(wz, PCy[c], QCy[c]);
             if (D >= 3) {
                 if (dz == 0) QCz[c] = cmul_r((T)(-1), PM[c]);
@@ -250,7 +248,8 @@ __device__ __forceinline__ void fields_std(Get get, const StdConst<T> &sc, T m, 
     for (int c = 0; c < NC; ++c) {
         GC[c].x = -sc.kc * QM[c].y; GC[c].y = sc.kc * QM[c].x;             // i kc QM
         if (WV) {
-            GM[c] = cmul_r(-sc.km, QW[c]);                                   // weights carry m beta + V
+            const int sb = Beta<D>::s(c) > 0 ? 0 : 1;
+            GM[c] = cfma_r(wb[sb], QCx[c], cmul_r(wa[sb], QM[c]));          // weights carry m beta + V
         } else {
             const T f = Beta<D>::s(c) > 0 ? -m * sc.km : m * sc.km;          // -beta m km
             GM[c] = cmul_r(f, QM[c]);
@@ -265,10 +264,10 @@ __device__ __forceinline__ void fields_std(Get get, const StdConst<T> &sc, T m, 
 // the x stencils of the RY + 2 rows are computed once and shared.
 // get(q, dx): node of row q (0 .. RY+1) and column dx (0 .. 2).
 template <int NC, typename T, bool WV, int RY, typename Get>
-__device__ __forceinline__ void fields_std_rows(Get get, const StdConst<T> &sc, T m, const T (&wx)[2][3],
+__device__ __forceinline__ void fields_std_rows(Get get, const StdConst<T> &sc, T m, const T (&wa)[2], const T (&wb)[2],
                                                 typename C2<T>::type (*GC)[NC], typename C2<T>::type (*GM)[NC]) {
     using V = typename C2<T>::type;
-    V rM[RY + 2][NC], rC[RY + 2][NC], rW[WV ? RY + 2 : 1][NC];
+    V rM[RY + 2][NC], rC[RY + 2][NC];
 #pragma unroll
     for (int q = 0; q < RY + 2; ++q) {
         const NodeV<NC, T> n0 = get(q, 0), n1 = get(q, 1), n2 = get(q, 2);
@@ -277,10 +276,6 @@ __device__ __forceinline__ void fields_std_rows(Get get, const StdConst<T> &sc, 
             const V x0 = n0.c[c], x1 = n1.c[c], x2 = n2.c[c];
             rM[q][c].x = fma((T)4, x1.x, x0.x + x2.x); rM[q][c].y = fma((T)4, x1.y, x0.y + x2.y);
             rC[q][c].x = x2.x - x0.x; rC[q][c].y = x2.y - x0.y;
-            if (WV) {
-                const int sb = Beta<2>::s(c) > 0 ? 0 : 1;
-                rW[WV ? q : 0][c] = cfma_r(wx[sb][0], x0, cfma_r(wx[sb][1], x1, cmul_r(wx[sb][2], x2)));
-            }
         }
     }
 #pragma unroll
@@ -293,8 +288,8 @@ __device__ __forceinline__ void fields_std_rows(Get get, const StdConst<T> &sc, 
             PCy[c] = csub(rM[r + 2][c], rM[r][c]);
             GC[r][c].x = -sc.kc * PM[c].y; GC[r][c].y = sc.kc * PM[c].x;
             if (WV) {
-                const V PW = cfma_r((T)4, rW[WV ? r + 1 : 0][c], cadd(rW[WV ? r : 0][c], rW[WV ? r + 2 : 0][c]));
-                GM[r][c] = cmul_r(-sc.km, PW);
+                const int sb = Beta<2>::s(c) > 0 ? 0 : 1;
+                GM[r][c] = cfma_r(wb[sb], PCx[c], cmul_r(wa[sb], PM[c]));
             } else {
                 const T f = Beta<2>::s(c) > 0 ? -m * sc.km : m * sc.km;
                 GM[r][c] = cmul_r(f, PM[c]);
@@ -362,10 +357,10 @@ __device__ __forceinline__ void apply_pipe_tile(const OpParams &p, const typenam
     }
     all_std = all_std && valid[0];
     const StdConst<T> sc = std_const<D, T>(p);
-    T wxs[2][3];     // x weights (m beta + V) of the standard path, h_x / 6 folded into StdConst
+    T wa[2], wb[2];  // mass-plus-potential weights of the standard path (fields_std), h_x / 6 in StdConst
     for (int sb = 0; sb < 2; ++sb) {
         const T wl = valid[0] ? k.wl[sb] : (T)0, wr = valid[0] ? k.wr[sb] : (T)0;
-        wxs[sb][0] = wl; wxs[sb][1] = 2 * (wl + wr); wxs[sb][2] = wr;
+        wa[sb] = (T)(-0.5) * sc.km * (wl + wr); wb[sb] = (T)(-0.5) * sc.km * (wr - wl);
     }
     CopyPlan<D, NC, T, TV> cplan;
     make_copy_plan<D, NC, T, TV>(p, x0, y0, z0, cplan);
@@ -407,19 +402,19 @@ __device__ __forceinline__ void apply_pipe_tile(const OpParams &p, const typenam
                     for (int c = 0; c < NC; ++c) { GC[r][c] = cz<V>(); GM[r][c] = cz<V>(); }
             } else if (RY > 1) {
                 auto getq = [&](int q, int dx) { return smem_node<NC, T>(slot, c0 + q * S::BX + dx); };
-                fields_std_rows<NC, T, !NOV, RY>(getq, sc, (T)p.m, wxs, GC, GM);
+                fields_std_rows<NC, T, !NOV, RY>(getq, sc, (T)p.m, wa, wb, GC, GM);
             } else {
                 auto get = [&](int q) {
                     const int dz = q / (3 * NY), dy = (q / 3) % NY, dx = q % 3;
                     return smem_node<NC, T>(slot, c0 + (dz * S::BY + dy) * S::BX + dx);
                 };
-                fields_std<D, NC, T, !NOV>(get, sc, (T)p.m, wxs, GC[0], GM[0]);
+                fields_std<D, NC, T, !NOV>(get, sc, (T)p.m, wa, wb, GC[0], GM[0]);
             }
             return;
         }
         if (have && RY > 1 && all_std) {
             auto getq = [&](int q, int dx) { return smem_node<NC, T>(slot, c0 + q * S::BX + dx); };
-            fields_std_rows<NC, T, !NOV, RY>(getq, sc, (T)p.m, wxs, GC, GM);
+            fields_std_rows<NC, T, !NOV, RY>(getq, sc, (T)p.m, wa, wb, GC, GM);
             return;
         }
 #pragma unroll
@@ -431,7 +426,7 @@ __device__ __forceinline__ void apply_pipe_tile(const OpParams &p, const typenam
                     return smem_node<NC, T>(slot, cr + (dz * S::BY + dy) * S::BX + dx);
                 };
                 if (stdn[r]) {
-                    fields_std<D, NC, T, !NOV>(get, sc, (T)p.m, wxs, GC[r], GM[r]);
+                    fields_std<D, NC, T, !NOV>(get, sc, (T)p.m, wa, wb, GC[r], GM[r]);
                 } else {
                     NodeCoef<D, T> kr;
                     if (r == 0) kr = k;

@@ -7,12 +7,13 @@
 // two time stencils through running accumulators).  What changes is the work
 // per thread: a thread owns RZ consecutive z outputs at one (x, y).  For each
 // staged time plane it walks the RZ + 2 z-slices of its column once: per slice
-// the x and y stencils of the 3 x 3 (x, y) neighbourhood give four fields
-// (M_x M_y, C_x M_y, M_x C_y and the potential-weighted M_x M_y), kept for the
-// last three slices; when a slice arrives, the z stencils of the output below it
-// are completed from the window.  Each staged node and each x-y stencil then
-// serves up to three outputs instead of one: about half the shared-memory loads
-// and floating-point work of one output per thread.
+// the x and y stencils of the 3 x 3 (x, y) neighbourhood give three fields
+// (M_x M_y, C_x M_y, M_x C_y; the x-only potential needs no fourth, see
+// fields_std), kept for the last three slices; when a slice
+// arrives, the z stencils of the output below it are completed from the
+// window.  Each staged node and each x-y stencil then serves up to three
+// outputs instead of one: about half the shared-memory loads and
+// floating-point work of one output per thread.
 //
 // Planes are staged by cp.async into a ring of shared-memory slots; the copy
 // sources of the CTA's box (byte offset in a layer, -1 outside a Dirichlet wall)
@@ -37,15 +38,14 @@ struct ZblkShape {
 };
 
 // The x-y fields of one z-slice for the thread's (x, y): unscaled sums
-//   FM = [1,4,1]_y [1,4,1]_x,  FCx = [1,4,1]_y [-1,0,1]_x,  FCy = [-1,0,1]_y [1,4,1]_x,
-//   FW = [1,4,1]_y (x weights w_l, 2 (w_l + w_r), w_r)   (WV only).
-template <typename T, bool WV>
+//   FM = [1,4,1]_y [1,4,1]_x,  FCx = [1,4,1]_y [-1,0,1]_x,  FCy = [-1,0,1]_y [1,4,1]_x.
+template <typename T>
 struct ZFields {
-    typename C2<T>::type M[4], Cx[4], Cy[4], W[WV ? 4 : 1];
+    typename C2<T>::type M[4], Cx[4], Cy[4];
 };
 
-template <typename T, bool WV, typename Get>
-__device__ __forceinline__ void zslice_fields(Get get, const T (&wx)[2][3], ZFields<T, WV> &F) {
+template <typename T, typename Get>
+__device__ __forceinline__ void zslice_fields(Get get, ZFields<T> &F) {
     using V = typename C2<T>::type;
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy) {
@@ -64,21 +64,16 @@ __device__ __forceinline__ void zslice_fields(Get get, const T (&wx)[2][3], ZFie
                 F.Cx[c] = cfma_r(wy, rC, F.Cx[c]);
                 if (dy == 2) F.Cy[c] = cadd(F.Cy[c], rM);
             }
-            if (WV) {
-                const int sb = Beta<3>::s(c) > 0 ? 0 : 1;
-                const V rW = cfma_r(wx[sb][0], x0, cfma_r(wx[sb][1], x1, cmul_r(wx[sb][2], x2)));
-                if (dy == 0) F.W[WV ? c : 0] = rW;
-                else F.W[WV ? c : 0] = cfma_r(wy, rW, F.W[WV ? c : 0]);
-            }
         }
     }
 }
 
 // G_C' and G_M' (scaled as in apply_pipe.cuh) of the output whose z-slices are A, B, C.
+// WV: G_M' = a QM + b QCx with the x-only potential weights of fields_std.
 template <typename T, bool WV>
-__device__ __forceinline__ void zcombine(const ZFields<T, WV> &A, const ZFields<T, WV> &Bf, const ZFields<T, WV> &Cf,
-                                         const StdConst<T> &sc, T m, typename C2<T>::type *GC,
-                                         typename C2<T>::type *GM) {
+__device__ __forceinline__ void zcombine(const ZFields<T> &A, const ZFields<T> &Bf, const ZFields<T> &Cf,
+                                         const StdConst<T> &sc, T m, const T (&wa)[2], const T (&wb)[2],
+                                         typename C2<T>::type *GC, typename C2<T>::type *GM) {
     using V = typename C2<T>::type;
     V QCx[4], QCy[4], QCz[4];
 #pragma unroll
@@ -91,8 +86,8 @@ __device__ __forceinline__ void zcombine(const ZFields<T, WV> &A, const ZFields<
         QCz[c] = csub(Cf.M[c], A.M[c]);
         GC[c].x = -sc.kc * QM.y; GC[c].y = sc.kc * QM.x;
         if (WV) {
-            const V QW = cadd(cfma_r((T)4, Bf.W[WV ? c : 0], A.W[WV ? c : 0]), Cf.W[WV ? c : 0]);
-            GM[c] = cmul_r(-sc.km, QW);
+            const int sb = Beta<3>::s(c) > 0 ? 0 : 1;
+            GM[c] = cfma_r(wb[sb], QCx[c], cmul_r(wa[sb], QM));
         } else {
             const T f = Beta<3>::s(c) > 0 ? -m * sc.km : m * sc.km;
             GM[c] = cmul_r(f, QM);
@@ -103,48 +98,23 @@ __device__ __forceinline__ void zcombine(const ZFields<T, WV> &A, const ZFields<
     add_i_alpha<4>(2, sc.ka[2], QCz, GM);
 }
 
-template <typename T, int RZ, bool NOV>
-__global__ void __launch_bounds__(ZblkShape<T, RZ>::NTHR, 2)
-apply_zblk_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typename C2<T>::type *__restrict__ y,
-                  int64_t tiles_x, int64_t tiles_y) {
+// The plane loop of one CTA.
+template <typename T, int RZ, bool WV>
+__device__ __forceinline__ void zblk_planes(const OpParams &p, const typename C2<T>::type *__restrict__ x,
+                                            typename C2<T>::type *__restrict__ y, char *ring, const int *src_tab,
+                                            int64_t x0, int64_t y0, int64_t z0, int64_t t0, int64_t t1,
+                                            const StdConst<T> &sc, const T (&wa)[2], const T (&wb)[2]) {
     using V = typename C2<T>::type;
     using S = ZblkShape<T, RZ>;
-    constexpr bool WV = !NOV;
-    extern __shared__ __align__(16) char smz[];
-    char *ring = smz;
-    int *src_tab = reinterpret_cast<int *>(smz + S::STAGES * S::SLOT);
-    const int64_t tile = blockIdx.x, chunk = blockIdx.y;
-    const int64_t x0 = (tile % tiles_x) * S::TX;
-    const int64_t y0 = ((tile / tiles_x) % tiles_y) * S::TY;
-    const int64_t z0 = (tile / (tiles_x * tiles_y)) * RZ;
     const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
     const int64_t ix = x0 + tx, iy = y0 + ty;
     const int64_t nx = p.ax[0].n, ny = p.ax[1].n, nz = p.ax[2].n;
     const int64_t N = p.nt;
-    const int64_t t0 = 1 + chunk * S::TT;
-    const int64_t t1 = min(t0 + (int64_t)S::TT, N + 1);
+    const bool colv = ix < nx && iy < ny;
     const int nplanes = (int)(t1 - t0 + 2);
     const int64_t pfirst = t0 - 1;
     const int64_t plane_elems = nx * ny * nz * 4;
     const size_t plane_bytes = (size_t)plane_elems * sizeof(V);
-    // copy sources of the box, once per CTA
-    for (int b = threadIdx.x; b < S::BOX; b += S::NTHR) {
-        const int bx = b % S::BX, by = (b / S::BX) % S::BY, bz = b / (S::BX * S::BY);
-        const int64_t gx = axis_nbr(p.ax[0], x0 - 1 + bx);
-        const int64_t gy = axis_nbr(p.ax[1], y0 - 1 + by);
-        const int64_t gz = axis_nbr(p.ax[2], z0 - 1 + bz);
-        src_tab[b] = (gx >= 0 && gy >= 0 && gz >= 0) ? (int)(((gz * ny + gy) * nx + gx) * S::NODE_BYTES) : -1;
-    }
-    __syncthreads();
-    const bool colv = ix < nx && iy < ny;
-    NodeCoef<3, T> k;
-    if (colv) node_coef<3, T>(p, ix, iy, z0 < nz ? z0 : 0, k);
-    const StdConst<T> sc = std_const<3, T>(p);
-    T wxs[2][3];
-    for (int sb = 0; sb < 2; ++sb) {
-        const T wl = colv ? k.wl[sb] : (T)0, wr = colv ? k.wr[sb] : (T)0;
-        wxs[sb][0] = wl; wxs[sb][1] = 2 * (wl + wr); wxs[sb][2] = wr;
-    }
     const int i_lo = (int)max((int64_t)0, 1 - pfirst);
     const int i_hi = (int)min((int64_t)(nplanes - 1), N - pfirst);
     const int i_last = (int)(N - pfirst);
@@ -183,21 +153,21 @@ apply_zblk_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
         const char *slot = ring + (size_t)si * S::SLOT;
         si = si + 1 == S::STAGES ? 0 : si + 1;
         const bool last = i >= i_last;
-        ZFields<T, WV> F0, F1, F2;
+        ZFields<T> F0, F1, F2;
 #pragma unroll
         for (int bz = 0; bz < RZ + 2; ++bz) {
-            ZFields<T, WV> &F = (bz % 3 == 0) ? F0 : ((bz % 3 == 1) ? F1 : F2);
+            ZFields<T> &F = (bz % 3 == 0) ? F0 : ((bz % 3 == 1) ? F1 : F2);
             if (have) {
                 auto get = [&](int dy, int dx) { return smem_node<4, T>(slot, (bz * S::BY + dy) * S::BX + cbase + dx); };
-                zslice_fields<T, WV>(get, wxs, F);
+                zslice_fields<T>(get, F);
             }
             if (bz >= 2) {
                 const int r = bz - 2;
                 V GC[4], GM[4];
                 if (have) {
-                    const ZFields<T, WV> &A = ((bz - 2) % 3 == 0) ? F0 : (((bz - 2) % 3 == 1) ? F1 : F2);
-                    const ZFields<T, WV> &Bm = ((bz - 1) % 3 == 0) ? F0 : (((bz - 1) % 3 == 1) ? F1 : F2);
-                    zcombine<T, WV>(A, Bm, F, sc, (T)p.m, GC, GM);
+                    const ZFields<T> &A = ((bz - 2) % 3 == 0) ? F0 : (((bz - 2) % 3 == 1) ? F1 : F2);
+                    const ZFields<T> &Bm = ((bz - 1) % 3 == 0) ? F0 : (((bz - 1) % 3 == 1) ? F1 : F2);
+                    zcombine<T, WV>(A, Bm, F, sc, (T)p.m, wa, wb, GC, GM);
                 } else {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) { GC[c] = cz<V>(); GM[c] = cz<V>(); }
@@ -221,6 +191,46 @@ apply_zblk_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typena
         if (i >= 2) ydst += plane_bytes;
     }
     cp_async_wait<0>();
+}
+
+template <typename T, int RZ, bool NOV>
+__global__ void __launch_bounds__(ZblkShape<T, RZ>::NTHR, 2)
+apply_zblk_kernel(OpParams p, const typename C2<T>::type *__restrict__ x, typename C2<T>::type *__restrict__ y,
+                  int64_t tiles_x, int64_t tiles_y) {
+    using S = ZblkShape<T, RZ>;
+    extern __shared__ __align__(16) char smz[];
+    char *ring = smz;
+    int *src_tab = reinterpret_cast<int *>(smz + S::STAGES * S::SLOT);
+    const int64_t tile = blockIdx.x, chunk = blockIdx.y;
+    const int64_t x0 = (tile % tiles_x) * S::TX;
+    const int64_t y0 = ((tile / tiles_x) % tiles_y) * S::TY;
+    const int64_t z0 = (tile / (tiles_x * tiles_y)) * RZ;
+    const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
+    const int64_t ix = x0 + tx, iy = y0 + ty;
+    const int64_t nx = p.ax[0].n, ny = p.ax[1].n, nz = p.ax[2].n;
+    const int64_t t0 = 1 + chunk * S::TT;
+    const int64_t t1 = min(t0 + (int64_t)S::TT, p.nt + 1);
+    // copy sources of the box, once per CTA
+    for (int b = threadIdx.x; b < S::BOX; b += S::NTHR) {
+        const int bx = b % S::BX, by = (b / S::BX) % S::BY, bz = b / (S::BX * S::BY);
+        const int64_t gx = axis_nbr(p.ax[0], x0 - 1 + bx);
+        const int64_t gy = axis_nbr(p.ax[1], y0 - 1 + by);
+        const int64_t gz = axis_nbr(p.ax[2], z0 - 1 + bz);
+        src_tab[b] = (gx >= 0 && gy >= 0 && gz >= 0) ? (int)(((gz * ny + gy) * nx + gx) * S::NODE_BYTES) : -1;
+    }
+    __syncthreads();
+    const bool colv = ix < nx && iy < ny;
+    const StdConst<T> sc = std_const<3, T>(p);
+    T wa[2] = {(T)0, (T)0}, wb[2] = {(T)0, (T)0};
+    if (!NOV && colv) {
+        NodeCoef<3, T> k;
+        node_coef<3, T>(p, ix, iy, z0 < nz ? z0 : 0, k);
+        for (int sb = 0; sb < 2; ++sb) {
+            wa[sb] = (T)(-0.5) * sc.km * (k.wl[sb] + k.wr[sb]);
+            wb[sb] = (T)(-0.5) * sc.km * (k.wr[sb] - k.wl[sb]);
+        }
+    }
+    zblk_planes<T, RZ, !NOV>(p, x, y, ring, src_tab, x0, y0, z0, t0, t1, sc, wa, wb);
 }
 
 template <typename T, int RZ>
