@@ -208,21 +208,23 @@ typedef struct {
     int profile;            /* 1: time every kernel with CUDA events (one event between
                                consecutive kernels; ~10% overhead on small meshes) */
     int inner_cycles;       /* GMRES(m) cycles per refinement step (mixed only; 0 = until
-                               inner_rtol), default 1 */
+                               inner_rtol), default 1.  Cycles after the first restart from
+                               the inner residual r - A d computed with the FP32 operator; the
+                               refinement's residual b - A psi is always FP64 */
     int ortho;              /* Gram-Schmidt (default 0): 0 = classical, second pass only when the DGKS test
                                asks (norm fell below 1/sqrt 2 of its value before the pass);
                                1 = always two classical passes (CGS2); 2 = one classical pass,
                                never reorthogonalised (PETSc's default for GMRES) */
     int mixed_ortho;        /* mixed only: arithmetic of the inner Gram-Schmidt (default 2).  0 = double-FP32
                                (basis stored as FP32 hi/lo planes, 48-bit significand, error-free
-                               FP32 products and sums, FP64 reductions; needs inner_cycles = 1),
+                               FP32 products and sums, FP64 reductions),
                                1 = native FP64 (FP64 basis),
                                2 = FP32-stored basis (8 B per entry, half the traffic of 0) with
                                exact FP32 products and compensated sums: inner products of the
                                stored values err by about 2^-40 of ||v|| ||w||, updates are
                                rounded to FP32 once, each new basis vector is rounded to
                                FP32 once; from 4M unknowns the projection is fed by bulk
-                               asynchronous copies (needs inner_cycles = 1) */
+                               asynchronous copies */
     int method;             /* Krylov method: 0 = restarted GMRES(restart) (default),
                                1 = BiCGSTAB (van der Vorst 1992; FP64 only, mixed_precision
                                must be 0; iters counts BiCGSTAB steps of two applies each) */
@@ -233,7 +235,7 @@ typedef struct {
                                inner GMRES becomes flexible GMRES (Saad 1993): each Arnoldi step
                                applies the operator to z_j = M(v_j), the z_j are kept (FP32), and a
                                cycle's correction is Z y.  Needs mixed_precision = 1,
-                               mixed_ortho = 2, inner_cycles = 1, method = 0.
+                               mixed_ortho = 2, method = 0.
                                DST_PRECOND_CN_SWEEP2 applies the sweep twice per step,
                                z = M v + M (v - A M v); DST_PRECOND_CN_LEARNED adds the
                                network attached by dst_set_learned_precond to the sweep.  dst_solve_batch honours it for the meshes
@@ -413,7 +415,11 @@ DST_API int dst_testing_fp32_arnoldi(int mode, int64_t n, int nvec, const void *
  * FP32 (the precision of the inner solve), the layer-solve factors in FP64
  * rounded to FP32.  Takes stream-ordered scratch of about one FP32 vector (plus
  * the factors, 32 NC^2 bytes per x node and frequency, on Dirichlet-x meshes).
- * Errors: DST_ERR_ARG (kind, mesh not covered), DST_ERR_OOM, DST_ERR_CUDA.
+ * kind DST_PRECOND_CN_SWEEP, or DST_PRECOND_CN_LEARNED (the sweep plus the
+ * learned correction below, with the network attached to the mesh by
+ * dst_set_learned_precond; two more FP32 vectors of scratch).
+ * Errors: DST_ERR_ARG (kind, mesh not covered, no network attached),
+ * DST_ERR_OOM, DST_ERR_CUDA.
  */
 enum { DST_PRECOND_NONE = 0, DST_PRECOND_CN_SWEEP = 1, DST_PRECOND_CN_SWEEP2 = 2, DST_PRECOND_CN_LEARNED = 3 };
 DST_API int dst_precond_apply(const dst_mesh *mesh, int kind, const void *v, void *z, void *stream);
@@ -435,8 +441,11 @@ DST_API int dst_energy(const dst_mesh *mesh, const void *psi, void *out, void *s
 /*
  * Learned correction of the sweep (DST_PRECOND_CN_LEARNED; no counterpart in
  * the paper, whose conclusion (Sec. 5) asks for a preconditioner):
- *     M(v) = M_CN(v) + s U(rho / s),   rho = v - A M_CN(v),  s = ||rho||,
- * with U a convolutional U-Net on the spacetime node grid (t, [z], [y], x) of the
+ *     M(v) = M_CN(v) + alpha U(rho / s),   rho = v - A M_CN(v),  s = ||rho||,
+ * with alpha the complex scale minimising ||rho - alpha A U(rho / s)||, taken
+ * afresh for every v (so no corrected direction leaves a larger residual than
+ * the sweep alone; one more FP32 operator apply per step), and U a
+ * convolutional U-Net on the spacetime node grid (t, [z], [y], x) of the
  * unknowns, 2 NC channels (Re, Im of each spinor component, i.e. the FP32
  * complex unknown vector read as [node][channel] floats).  Layers, in order
  * (conv3: kernel 3 in every grid axis, zero padding keeping the size; conv1:
@@ -464,10 +473,11 @@ DST_API int dst_energy(const dst_mesh *mesh, const void *psi, void *out, void *s
  *   pairs the method generates on the GPU: e standard normal (splitmix64 of
  *   seed and index), r = A e, z = M_CN(r), input rho = r - A z, target e - z;
  *   loss per step into loss_host (HOST, `steps` floats, may be NULL).  Then the
- *   output scale gamma of the correction, z += gamma s U(rho / s), is set to the
- *   least-squares factor <U, t> / ||U||^2 over 8 fresh pairs (0 if negative), so
- *   that on such pairs the scaled correction never leaves a larger error than
- *   the sweep alone.  The mesh must be one the sweep covers.  Synchronises.
+ *   output scale gamma of dst_unet_forward is set to the least-squares factor
+ *   <U, t> / ||U||^2 over 8 fresh pairs (0 if negative): a summary of how well
+ *   the network fits the error on such pairs (the solver takes its own scale
+ *   per application, above).  The mesh must be one the sweep covers.
+ *   Synchronises.
  * dst_unet_output_scale: the current gamma (1 after create / set_params).
  * dst_set_learned_precond: use `net` (NULL: none) in solves of this mesh with
  *   precond = DST_PRECOND_CN_LEARNED.  The mesh does not own it; solves that

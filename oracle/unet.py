@@ -29,10 +29,18 @@ D = 4 the convolution is, by its definition, the sum over the three time
 offsets of 3D convolutions of the shifted time slices.  Gradients come from
 torch autograd.
 
+Correction of the Crank-Nicolson sweep (``learned_correction``): with
+rho = v - A M_CN(v) and u = U(rho / ||rho||) (the network without the final
+rescaling), M(v) = M_CN(v) + alpha u, alpha the complex least-squares scale
+minimising ||rho - alpha A u|| (``ls_scale``), so that ||v - A M(v)|| never
+exceeds ||v - A M_CN(v)||.
+
 Only ``tests/`` imports this module.  Pinned by tests/test_oracle_unet.py:
 convolutions against a brute-force loop over the definition, pool and
 upsample as adjoint pairs, autograd gradients against finite differences,
-the homogeneity and the grid layout.
+the homogeneity and the grid layout; the least-squares scale against exact
+solutions and its normal equation, and the correction reducing to the sweep
+for a zero output layer and never raising the residual.
 """
 
 import math
@@ -157,4 +165,28 @@ def preconditioner(mesh, params):
     def M(v):
         with torch.no_grad():
             return from_grid(mesh, apply(params, to_grid(mesh, v)))[0]
+    return M
+
+
+def ls_scale(Au, rho):
+    """Complex alpha minimising ||rho - alpha Au|| over alpha: <Au, rho> / <Au, Au>
+    (conjugate-linear in the first argument); 0 when Au = 0."""
+    aa = np.vdot(Au, Au).real
+    return complex(np.vdot(Au, rho) / aa) if aa > 0 else 0j
+
+
+def learned_correction(mesh, params, A, sweep):
+    """Callable v -> M_CN(v) + alpha U(rho / ||rho||) on complex unknown vectors,
+    rho = v - A M_CN(v), alpha = ls_scale(A U, rho); A a sparse matrix, sweep the
+    callable of precond.crank_nicolson_sweep."""
+    def M(v):
+        v = np.asarray(v, dtype=np.complex128)
+        z0 = sweep(v)
+        rho = v - A @ z0
+        nrm = np.linalg.norm(rho)
+        if nrm == 0:
+            return z0
+        with torch.no_grad():
+            u = from_grid(mesh, forward(params, to_grid(mesh, rho / nrm)))[0]
+        return z0 + ls_scale(A @ u, rho) * u
     return M

@@ -37,7 +37,7 @@ struct Workspace {
     int64_t n;
     int m;
     bool mixed;
-    double2 *V, *b, *tmp, *d, *r64, *h1, *h2;
+    double2 *V, *b, *tmp, *d, *r64, *rin, *h1, *h2;   // rin: inner residual between cycles of one refinement
     float2 *x32, *y32;
     double *nrm;
     unsigned *tickets;     // [2] zero counters of the in-kernel reductions
@@ -75,6 +75,7 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w, int precond
     const size_t ot = take(sizeof(double2) * n);
     const size_t od = mixed ? take(sizeof(double2) * n) : 0;
     const size_t or64 = mixed ? take(sizeof(double2) * n) : 0;
+    const size_t orin = mixed ? take(sizeof(double2) * n) : 0;
     const size_t ox32 = mixed ? take(sizeof(float2) * n) : 0;
     const size_t oy32 = mixed ? take(sizeof(float2) * n) : 0;
     const size_t oh1 = take(sizeof(double2) * DST_MAX_VEC);
@@ -114,6 +115,7 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w, int precond
     w.tmp = (double2 *)(base + ot);
     w.d = mixed ? (double2 *)(base + od) : nullptr;
     w.r64 = mixed ? (double2 *)(base + or64) : nullptr;
+    w.rin = mixed ? (double2 *)(base + orin) : nullptr;
     w.x32 = mixed ? (float2 *)(base + ox32) : nullptr;
     w.y32 = mixed ? (float2 *)(base + oy32) : nullptr;
     w.h1 = (double2 *)(base + oh1);
@@ -545,7 +547,8 @@ struct Solver {
     }
 
     // z = M(v) with the Crank-Nicolson sweep; the second variant adds M(v - A M(v)),
-    // with tmp (a free FP32 vector: the next basis slot) holding A M(v).
+    // the learned one a correction computed from rho = v - A M(v); tmp is a free
+    // FP32 vector (the next basis slot), holding A M(v) and then scratch.
     int precondition(const float2 *v, float2 *z, float2 *tmp) {
         const int64_t n = w.n;
         const double dn = (double)n;
@@ -557,8 +560,13 @@ struct Solver {
                       [&] { return dst_internal_apply(mesh, DST_FP32, z, tmp, s); })))
             return rc;
         if ((rc = run(K_MISC, 1, 24.0 * dn, 2.0 * dn, [&] { return dst_k_sub_f32(n, v, tmp, w.pr, s); }))) return rc;
-        if (precond == DST_PRECOND_CN_LEARNED)        // z += s U(rho / s), rho = v - A M_CN(v)
-            return run(K_PRECOND, 30, 0.0, 0.0, [&] { return dst_internal_unet_correct(mesh->unet, w.pr, z, s); });
+        if (precond == DST_PRECOND_CN_LEARNED) {      // z += alpha U(rho / ||rho||), rho = v - A M_CN(v)
+            int nk = 0;
+            rc = run(K_PRECOND, 0, 0.0, 0.0,
+                     [&] { return dst_internal_unet_correct(mesh->unet, mesh, w.pr, z, tmp, s, &nk); });
+            prof.launches[K_PRECOND] += nk;
+            return rc;
+        }
         if ((rc = run(K_PRECOND, plan.has_fft ? 4 : 3, sweep_bytes, 0.0,
                       [&] { return dst_sweep_apply(plan, n, w.pr, w.pz2, s); })))
             return rc;
@@ -916,9 +924,12 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
             if ((rc = sv.sync())) return rc;
             rnorm = std::sqrt(sv.w.host[0]);
         }
-        // df32 Gram-Schmidt needs the correction to be one cycle from d = 0;
-        // the r64 residual norm^2 must sit in nrm[2] for the first split
-        const bool use_df = o.mixed_ortho != 1 && o.inner_cycles == 1;
+        // df32 / FP32-stored Gram-Schmidt runs each cycle from a correction of 0 on a
+        // right-hand side whose norm^2 sits in nrm[2]: the refinement residual r64
+        // first, then for further cycles of the same refinement the inner residual
+        // r64 - A d with the FP32 operator, the cycle's correction added to d
+        const bool use_df = o.mixed_ortho != 1;
+        const int cycles = o.inner_cycles > 0 ? o.inner_cycles : 0x7fffffff;
         if (!o.use_initial_guess) {
             DST_CUDA_TRY(cudaMemcpyAsync(sv.w.nrm + 2, sv.w.nrm + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
         }
@@ -928,9 +939,19 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
             double inner_beta;
             DST_CUDA_TRY(cudaMemsetAsync(sv.w.d, 0, sizeof(double2) * n, s));
             const double itol = std::max(o.inner_rtol * rnorm, 0.5 * tol);
-            if (use_df)
+            if (use_df) {
                 rc = sv.cycle_df(sv.w.d, sv.w.r64, 2, rnorm, itol, o.max_iters, o.mixed_ortho == 0);
-            else
+                for (int c = 1; rc == DST_OK && c < cycles && sv.resid_est > itol && sv.iters < o.max_iters; ++c) {
+                    if ((rc = sv.apply(DST_FP32, sv.w.d, sv.w.tmp))) return rc;
+                    if ((rc = sv.residual(sv.w.r64, sv.w.tmp, sv.w.rin, sv.w.nrm + 2))) return rc;
+                    DST_CUDA_TRY(cudaMemcpyAsync(sv.w.host, sv.w.nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+                    if ((rc = sv.sync())) return rc;
+                    const double rin = std::sqrt(sv.w.host[0]);
+                    if (!std::isfinite(rin)) return DST_ERR_NAN;
+                    if (rin <= itol) break;
+                    rc = sv.cycle_df(sv.w.d, sv.w.rin, 2, rin, itol, o.max_iters, o.mixed_ortho == 0);
+                }
+            } else
                 rc = sv.gmres(DST_FP32, sv.w.d, sv.w.r64, true, itol, o.max_iters, inner_beta,
                               o.inner_cycles > 0 ? o.inner_cycles : 0x7fffffff);
             if (rc) return rc;
@@ -976,7 +997,7 @@ extern "C" int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, 
         o.mixed_ortho < 0 || o.mixed_ortho > 2 || o.inner_cycles < 0 || o.method < 0 || o.method > 1 ||
         (o.method == 1 && o.mixed_precision) || o.precond < 0 || o.precond > DST_PRECOND_CN_LEARNED ||
         (o.precond == DST_PRECOND_CN_LEARNED && !dst_internal_unet_fits(mesh->unet, mesh)) ||
-        (o.precond && (!o.mixed_precision || o.mixed_ortho != 2 || o.inner_cycles != 1 || o.method != 0))) {
+        (o.precond && (!o.mixed_precision || o.mixed_ortho != 2 || o.method != 0))) {
         rc = DST_ERR_ARG;
     } else if (!mesh->d_psi0) {
         rc = DST_ERR_STATE;

@@ -89,9 +89,12 @@ struct dst_mesh {
     dst_unet *unet;               // learned correction of the sweep preconditioner (not owned), or null
 };
 
-// The learned correction (unet.cu): z += s U(rho / s) with s = ||rho||; and
-// whether a network was built for this mesh's grid on its device.
-int dst_internal_unet_correct(dst_unet *u, const float2 *rho, float2 *z, cudaStream_t s);
+// The learned correction (unet.cu): z += alpha U(rho / ||rho||) with alpha the
+// complex least-squares scale minimising ||rho - alpha A U|| (tmp: a free FP32
+// vector for A U; *launches: kernels enqueued); and whether a network was
+// built for this mesh's grid on its device.
+int dst_internal_unet_correct(dst_unet *u, const dst_mesh *mesh, const float2 *rho, float2 *z, float2 *tmp,
+                              cudaStream_t s, int *launches);
 bool dst_internal_unet_fits(const dst_unet *u, const dst_mesh *mesh);
 
 // Testing hooks (dst_testing_set): the bulk-copy wait limit in force (the

@@ -36,6 +36,7 @@
 #include <cstring>
 #include <vector>
 
+#include "blas.h"
 #include "internal.h"
 #include "sweep.h"
 #include "fft.cuh"
@@ -59,7 +60,6 @@ __host__ __device__ inline cd cdiv(cd a, cd b) {
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ float2 caddf(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csubf(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 // acc + a * b
 __device__ __forceinline__ float2 cfmaf(float2 a, float2 b, float2 acc) {
@@ -661,8 +661,12 @@ int dst_sweep_apply(const SweepPlan &p, int64_t n_unknowns, const float2 *v, flo
 
 extern "C" int dst_precond_apply(const dst_mesh *mesh, int kind, const void *v, void *z, void *stream) {
     if (!mesh || !v || !z || v == z) return DST_ERR_ARG;
-    if (kind != DST_PRECOND_CN_SWEEP) {
+    if (kind != DST_PRECOND_CN_SWEEP && kind != DST_PRECOND_CN_LEARNED) {
         dst_internal_set_error_detail("dst_precond_apply: unknown preconditioner kind");
+        return DST_ERR_ARG;
+    }
+    if (kind == DST_PRECOND_CN_LEARNED && !dst_internal_unet_fits(mesh->unet, mesh)) {
+        dst_internal_set_error_detail("dst_precond_apply: no network for this mesh (dst_set_learned_precond)");
         return DST_ERR_ARG;
     }
     SweepPlan p;
@@ -670,13 +674,24 @@ extern "C" int dst_precond_apply(const dst_mesh *mesh, int kind, const void *v, 
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     void *scratch = nullptr;
-    const size_t bytes = dst_sweep_scratch_bytes(p, mesh->n_unknowns);
+    const int64_t n = mesh->n_unknowns;
+    const size_t sweep_bytes = (dst_sweep_scratch_bytes(p, n) + 255) & ~(size_t)255;
+    const size_t vec_bytes = ((size_t)n * sizeof(float2) + 255) & ~(size_t)255;
+    const size_t bytes = sweep_bytes + (kind == DST_PRECOND_CN_LEARNED ? 2 * vec_bytes : 0);
     if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return DST_ERR_OOM;
     }
     rc = dst_sweep_setup(mesh, p, scratch, s);
-    if (rc == DST_OK) rc = dst_sweep_apply(p, mesh->n_unknowns, (const float2 *)v, (float2 *)z, s);
+    if (rc == DST_OK) rc = dst_sweep_apply(p, n, (const float2 *)v, (float2 *)z, s);
+    if (rc == DST_OK && kind == DST_PRECOND_CN_LEARNED) {
+        float2 *tmp = reinterpret_cast<float2 *>((char *)scratch + sweep_bytes);
+        float2 *rho = reinterpret_cast<float2 *>((char *)scratch + sweep_bytes + vec_bytes);
+        int nk = 0;
+        rc = dst_internal_apply(mesh, DST_FP32, z, tmp, s);                 // rho = v - A M_CN(v)
+        if (rc == DST_OK) rc = dst_k_sub_f32(n, (const float2 *)v, tmp, rho, s);
+        if (rc == DST_OK) rc = dst_internal_unet_correct(mesh->unet, mesh, rho, (float2 *)z, tmp, s, &nk);
+    }
     cudaFreeAsync(scratch, s);
     return rc;
 }

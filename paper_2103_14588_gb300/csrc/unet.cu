@@ -253,6 +253,50 @@ __global__ void dot_kernel(int64_t n, const float *__restrict__ y, const float *
     if (threadIdx.x == 0) { acc[0] += r1[0]; acc[1] += r2[0]; }
 }
 
+// Partial sums of <a, r> = sum conj(a_i) r_i (re, im) and ||a||^2 over complex
+// vectors, one triple per CTA (FP64), for the least-squares scale of the correction.
+constexpr int LS_PARTS = 304;
+__global__ void __launch_bounds__(256) ls_partials_kernel(int64_t n, const float2 *__restrict__ a,
+                                                          const float2 *__restrict__ r, double *__restrict__ part) {
+    __shared__ double red[3][256];
+    double re = 0.0, im = 0.0, aa = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 ai = a[i], ri = r[i];
+        re += (double)ai.x * ri.x + (double)ai.y * ri.y;
+        im += (double)ai.x * ri.y - (double)ai.y * ri.x;
+        aa += (double)ai.x * ai.x + (double)ai.y * ai.y;
+    }
+    red[0][threadIdx.x] = re; red[1][threadIdx.x] = im; red[2][threadIdx.x] = aa;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) part[3 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// z += alpha y with alpha = <a, r> / ||a||^2 from the partials (0 when a = 0);
+// every CTA sums the partials in the same order, so all use the same alpha.
+__global__ void __launch_bounds__(256) ls_axpy_kernel(int64_t n, int nparts, const double *__restrict__ part,
+                                                      const float2 *__restrict__ y, float2 *__restrict__ z) {
+    __shared__ float2 alpha;
+    if (threadIdx.x == 0) {
+        double re = 0.0, im = 0.0, aa = 0.0;
+        for (int b = 0; b < nparts; ++b) { re += part[3 * b]; im += part[3 * b + 1]; aa += part[3 * b + 2]; }
+        alpha = aa > 0.0 ? make_float2((float)(re / aa), (float)(im / aa)) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float2 yi = y[i];
+        float2 zi = z[i];
+        zi.x += alpha.x * yi.x - alpha.y * yi.y;
+        zi.y += alpha.x * yi.y + alpha.y * yi.x;
+        z[i] = zi;
+    }
+}
+
 // standard normal pairs from splitmix64 of (seed, index) by Box-Muller
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z += 0x9E3779B97F4A7C15ull;
@@ -293,6 +337,7 @@ struct dst_unet {
     float *gamma;                                          // device scalar: output scale of the correction
     double gamma_host;
     double *dscr;                                          // device doubles: [0] sum sq, [1] loss, [2] target sumsq
+    double *part;                                          // LS_PARTS x 3 partial sums of the correction's scale
     int64_t act_floats;
     void *mem;
     size_t mem_bytes;
@@ -373,6 +418,7 @@ static int unet_create(const dst_mesh *mesh, dst_unet **out) {
     const size_t o_gs1 = take(sizeof(float) * N1 * 16), o_gs2 = take(sizeof(float) * N2 * 32);
     const size_t o_gm = take(sizeof(float) * big);
     const size_t o_sc = take(sizeof(float) * 4), o_ds = take(sizeof(double) * 4);
+    const size_t o_pt = take(sizeof(double) * 3 * LS_PARTS);
     if (cudaMalloc(&u->mem, total) != cudaSuccess) {
         cudaGetLastError();
         delete u;
@@ -401,6 +447,7 @@ static int unet_create(const dst_mesh *mesh, dst_unet **out) {
     u->scale = (float *)(b + o_sc);
     u->gamma = u->scale + 1;
     u->dscr = (double *)(b + o_ds);
+    u->part = (double *)(b + o_pt);
     cudaError_t e = cudaMemset(u->mem, 0, total);
     const float one = 1.0f;
     if (e == cudaSuccess) e = cudaMemcpy(u->gamma, &one, sizeof(float), cudaMemcpyHostToDevice);
@@ -579,13 +626,21 @@ static int loss_grad(dst_unet *u, const float *x, const float *t, cudaStream_t s
 
 // ---- preconditioner hook used by the solver --------------------------------------
 
-int dst_internal_unet_correct(dst_unet *u, const float2 *rho, float2 *z, cudaStream_t s) {
-    const int64_t n = u->grid[0].N * u->C;
+int dst_internal_unet_correct(dst_unet *u, const dst_mesh *mesh, const float2 *rho, float2 *z, float2 *tmp,
+                              cudaStream_t s, int *launches) {
+    const int64_t n = u->grid[0].N * u->C, nc = n / 2;
     const float *x = reinterpret_cast<const float *>(rho);
+    const float2 *y = reinterpret_cast<const float2 *>(u->y);
+    *launches = (u->packed ? 0 : NLAYER) + 2 + 15 + 1 + 2;
     int rc;
     if ((rc = norm_into_scale(u, x, n, s))) return rc;
     if ((rc = forward(u, x, u->scale, s))) return rc;
-    axpy_scaled_kernel<<<nblk(n), 256, 0, s>>>(n, u->scale, u->gamma, u->y, reinterpret_cast<float *>(z));
+    // the correction's scale for this input: alpha minimising ||rho - alpha A y||, so the
+    // corrected direction never leaves a larger residual than the sweep alone
+    if ((rc = dst_internal_apply(mesh, DST_FP32, y, tmp, s))) return rc;
+    const int parts = (int)std::min<int64_t>(LS_PARTS, (nc + 2047) / 2048);
+    ls_partials_kernel<<<parts, 256, 0, s>>>(nc, tmp, rho, u->part);
+    ls_axpy_kernel<<<nblk(nc), 256, 0, s>>>(nc, parts, u->part, y, z);
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }

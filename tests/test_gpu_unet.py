@@ -9,11 +9,13 @@ loss within 5e-2 relative; the gradient of every parameter tensor rel. L2 <=
 1e-1 and all of them together <= 5e-2.  A wrong tap order, channel index,
 transposition or sign gives O(1).
 
-Training on pairs the method generates (dst_unet_train), from a zero output
-layer (the corrected preconditioner starts as the sweep, loss 1), brings the
-loss below 1; flexible GMRES with the trained correction reaches the exact (LU)
-solution, and the test prints how many steps the correction saves (or costs)
-against the sweep alone.
+One application of the corrected preconditioner, M(v) = M_CN(v) + alpha
+U(rho / ||rho||) with alpha the least-squares scale of A U against rho, matches
+oracle.unet.learned_correction.  Training on pairs the method generates
+(dst_unet_train), from a zero output layer (the corrected preconditioner starts
+as the sweep, loss 1), brings the loss below 1; flexible GMRES with the trained
+correction reaches the exact (LU) solution, and the test prints how many steps
+the correction saves (or costs) against the sweep alone.
 """
 import numpy as np
 import pytest
@@ -108,6 +110,50 @@ def test_unet_forward_and_gradients_match_oracle(name, make):
             assert rel_l2(got_g[off:off + k], ref_g[off:off + k]) <= 1e-1, (n + suf, rel_l2(got_g[off:off + k],
                                                                                          ref_g[off:off + k]))
             off += k
+
+
+@pytest.mark.parametrize("name,make", [("1p1", lambda: W.plane_wave_1p1(n=20)), ("2p1", lambda: W.zb_2p1(n=10, nt=9))])
+def test_learned_application_matches_oracle(name, make):
+    """One application M(v) = M_CN(v) + alpha U(rho / ||rho||) (dst_precond_apply) against
+    oracle.unet.learned_correction with the network's BF16-rounded parameters, after a
+    short training on the GPU (so that the correction is a sizeable part of M(v)): the
+    sweep part to FP32 rounding, the correction to the network's BF16 rounding (5e-2 of
+    its size)."""
+    import torch
+    from oracle import operator as OOP, precond as PC, unet as U
+    from paper_2103_14588_gb300 import binding as B
+    w = make()
+    om = oracle_mesh(w)
+    A, _ = OOP.split(om, OOP.assemble(om, w.m, w.V), w.psi0)
+    A = A.tocsr()
+    sweep = PC.crank_nicolson_sweep(A, om.nt, om.n_spatial_nodes * om.nc)[0]
+    v = W.random_complex(om.n_unknowns, 17).astype(np.complex64)
+    z0 = sweep(v.astype(np.complex128))
+    with B.Mesh.from_workload(w) as mesh:
+        net = B.UNet(mesh.handle)
+        params = U.init_params(w.d, om.nc, seed=8)
+        params["out.w"].zero_()
+        net.set_params(_bf16(_flat(params)).astype(np.float32))
+        net.train(mesh.handle, steps=300, lr=1e-3, seed=5)
+        flat = _bf16(net.get_params())
+        vd = torch.from_numpy(v).cuda()
+        zd = torch.full_like(vd, complex("nan+nanj"))
+        with pytest.raises(B.DstError):                 # no network attached yet
+            B.dst_precond_apply(mesh.handle, B.DST_PRECOND_CN_LEARNED, vd, zd)
+        B.dst_set_learned_precond(mesh.handle, net)
+        B.dst_precond_apply(mesh.handle, B.DST_PRECOND_CN_LEARNED, vd, zd)
+        torch.cuda.synchronize()
+        got = zd.cpu().numpy()
+        B.dst_set_learned_precond(mesh.handle, None)
+        net.close()
+    ref = U.learned_correction(om, _unflat(w.d, om.nc, flat), A, sweep)(v.astype(np.complex128))
+    corr = np.linalg.norm(ref - z0) / np.linalg.norm(ref)
+    print("%s: correction %.3g of M(v), GPU vs oracle %.3g" % (name, corr, rel_l2(got, ref)))
+    assert corr > 1e-3                                      # the correction is really there
+    assert rel_l2(got, ref) <= 1e-4 + 5e-2 * corr, (rel_l2(got, ref), corr)
+    # the GPU's corrected direction leaves no larger residual than the sweep's
+    r_got = np.linalg.norm(v - A @ got.astype(np.complex128))
+    assert r_got <= np.linalg.norm(v - A @ z0) * (1 + 1e-4)
 
 
 def test_training_lowers_the_loss_and_the_correction_solves():

@@ -107,3 +107,53 @@ def test_homogeneity_and_zero():
     assert np.linalg.norm(Mr) > 0
     np.testing.assert_allclose(M(7.5 * r), 7.5 * Mr, rtol=1e-12, atol=1e-14)
     assert np.all(M(np.zeros_like(r)) == 0)
+
+
+# ---- the learned correction of the sweep ------------------------------------------
+
+def test_ls_scale_is_the_least_squares_solution():
+    """rho = alpha* Au + (a part orthogonal to Au) gives back alpha* (complex, so a
+    conjugate taken on the wrong side shows); the residual is orthogonal to Au;
+    Au = 0 gives 0."""
+    rng = np.random.default_rng(41)
+    n = 57
+    Au = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    a_star = 0.7 - 1.3j
+    r = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    r_perp = r - (np.vdot(Au, r) / np.vdot(Au, Au)) * Au       # Gram-Schmidt of r against Au
+    assert abs(np.vdot(Au, r_perp)) < 1e-12 * np.linalg.norm(Au) * np.linalg.norm(r)
+    assert abs(U.ls_scale(Au, a_star * Au) - a_star) < 1e-14
+    assert abs(U.ls_scale(Au, a_star * Au + r_perp) - a_star) < 1e-12
+    alpha = U.ls_scale(Au, r)
+    assert abs(np.vdot(Au, r - alpha * Au)) < 1e-12 * np.linalg.norm(Au) * np.linalg.norm(r)
+    assert U.ls_scale(np.zeros(n, complex), r) == 0
+
+
+def _sweep_system():
+    from oracle import operator as OP, precond as PC
+    rng = np.random.default_rng(12)
+    me = Mesh(1, [12, 1, 1, 8], [0, 0, 0, 0], [4.0, 1.0, 1.0, 1.0], [PERIODIC])
+    psi0 = rng.standard_normal(me.spatial_shape) + 1j * rng.standard_normal(me.spatial_shape)
+    A, _ = OP.split(me, OP.assemble(me, 1.0, None), psi0)
+    A = A.tocsr()
+    return me, A, PC.crank_nicolson_sweep(A, me.nt, me.n_spatial_nodes * me.nc)[0]
+
+
+def test_learned_correction_reduces_to_the_sweep_and_never_raises_the_residual():
+    me, A, sweep = _sweep_system()
+    rng = np.random.default_rng(13)
+    v = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    z0 = sweep(v)
+    params = U.init_params(me.d, me.nc, seed=4)
+    zero_out = dict(params)
+    zero_out["out.w"] = torch.zeros_like(params["out.w"])
+    zero_out["out.b"] = torch.zeros_like(params["out.b"])
+    assert np.array_equal(U.learned_correction(me, zero_out, A, sweep)(v), z0)
+    z = U.learned_correction(me, params, A, sweep)(v)
+    r0 = np.linalg.norm(v - A @ z0)
+    r1 = np.linalg.norm(v - A @ z)
+    assert not np.allclose(z, z0)
+    assert r1 <= r0 * (1 + 1e-12)
+    # the residual left is orthogonal to A u, u the correction's direction
+    u = (z - z0)
+    assert abs(np.vdot(A @ u, v - A @ z)) < 1e-10 * np.linalg.norm(A @ u) * r1
