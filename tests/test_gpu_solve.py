@@ -139,6 +139,26 @@ def test_mixed_until_inner_tolerance_and_cgs2(torch, B, ortho):
         assert st["reorths"] == st["iters"]
 
 
+@pytest.mark.parametrize("mixed_ortho,precond", [(2, 0), (0, 0), (2, 1)])
+def test_several_inner_cycles_per_refinement(torch, B, mixed_ortho, precond):
+    """Two and four GMRES(m) cycles per refinement step, the cycles after the first
+    restarting from the inner residual with the FP32 operator: the same solution, the
+    FP64 residual below rtol, and fewer refinement steps (FP64 applies) than one
+    cycle per refinement."""
+    w = W.zb_2p1(n=16, nt=16) if precond else W.random_mesh(2, [12, 10, 1, 14], [P, P], seed=81)
+    ref, _, _ = _exact(w)
+    base = dict(restart=10, rtol=1e-10, max_iters=50000, mixed_precision=1, mixed_ortho=mixed_ortho,
+                inner_rtol=1e-4, max_refine=400, precond=precond)
+    x1, s1 = _solve(torch, B, w, inner_cycles=1, **base)
+    assert s1["status"] == 0 and rel_l2(x1, ref) <= 1e-8
+    for k in (2, 4):
+        x, st = _solve(torch, B, w, inner_cycles=k, **base)
+        assert st["status"] == 0 and st["rel_resid_true"] <= 1e-10
+        assert rel_l2(x, ref) <= 1e-8
+        assert st["refinements"] < s1["refinements"], (k, st["refinements"], s1["refinements"])
+        assert st["iters"] <= 1.3 * s1["iters"] + 20, (k, st["iters"], s1["iters"])
+
+
 def test_full_size_fp64_solve_matches_oracle_step_count(torch, B):
     """The FP64 GMRES(30) solve of the 96^2 x 96 Zitterbewegung system takes the
     number of Arnoldi steps the oracle's own GMRES took (recorded by
