@@ -363,7 +363,7 @@ DST_API int dst_observables(const dst_mesh *mesh, const void *psi, double x0, vo
  * failure paths reachable from a test on a healthy GPU, with nothing faulted.
  * Process-wide settings, meant for tests only.
  *   DST_TEST_WAIT_LIMIT  value = tries a bulk-copy wait of the Arnoldi
- *                        projection makes before giving up; -1 restores the
+ *                        projection or update makes before giving up; -1 restores the
  *                        standard 2^22.  With 0 every wait gives up at once,
  *                        before its copy can have landed: the kernel stops
  *                        consuming, waits (standard limit) for the copies it
@@ -388,10 +388,11 @@ DST_API int dst_testing_set(int hook, int64_t value);
  *   mode 0: h = V^H w by the register-fed projection (h: DEVICE nvec FP64 complex);
  *   mode 1: the same by the bulk-copy fed projection;
  *   mode 2: w <- w - V h (h: DEVICE FP64 complex input), rounded to FP32 once,
- *           and *nrm2 (DEVICE double) = ||w||^2 of the stored result.
+ *           and *nrm2 (DEVICE double) = ||w||^2 of the stored result;
+ *   mode 3: the same update with the basis fed by bulk copies.
  * Products are exact and sums compensated: the error of h_j is about 2^-40 of
  * ||v_j|| ||w|| (measured with unit basis vectors).  Takes stream-ordered
- * scratch; mode 1 synchronises the stream.  Errors: DST_ERR_ARG, DST_ERR_OOM,
+ * scratch; modes 1 and 3 synchronise the stream.  Errors: DST_ERR_ARG, DST_ERR_OOM,
  * DST_ERR_CUDA (a bulk-copy wait that gave up).
  */
 DST_API int dst_testing_fp32_arnoldi(int mode, int64_t n, int nvec, const void *V, void *w, void *h, void *nrm2,

@@ -47,6 +47,11 @@ int dst_k_scale_df(int64_t n, float2 *v, const double *nrm2, cudaStream_t s, boo
 int dst_tma_projection_blocks(int64_t n);
 int dst_k_project_tma(int64_t n, int nvec, const float2 *V, const float2 *w, double2 *h, double2 *partials, int nblk,
                       cudaStream_t s, double *wnrm2, const double *gate, unsigned *ticket, double *err);
+// the update w -= V h (FP32-stored basis) with the basis fed by the same bulk
+// copies; partials: nblk doubles; gate / counter as in dst_k_update_df.
+int dst_k_update_tma(int64_t n, int nvec, const float2 *V, const double2 *h, float2 *w, double *nrm2,
+                     double *partials, int nblk, cudaStream_t s, const double *gate, double *counter,
+                     unsigned *ticket, double *err);
 int dst_k_split_f64_df(int64_t n, const double2 *src, const double *nrm2, float2 *dst, cudaStream_t s,
                        bool vlo = true);
 int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double2 *x, cudaStream_t s,

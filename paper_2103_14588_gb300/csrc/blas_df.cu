@@ -603,6 +603,184 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
     if (tid == 0) *ticket = 0u;
 }
 
+// The update w <- w - sum_j V_j h_j of update_f32_kernel (same per-entry
+// arithmetic: anchor max |w component| + sum_j |h_j|_1, the vectors in order,
+// rounded once), with the basis streamed through the bulk-copy ring of
+// project_tma_kernel: per chunk of the CTA's slice the consumers read w from
+// global memory into registers, take the chunks of all nvec vectors from the
+// ring, and store the result with its norm.  w is read and written once, every
+// basis vector read once.  Same failure handling as project_tma_kernel (a
+// consumer that meets a failed wait stops; the copies in flight are waited
+// for; *err = 1 and the chunks not reached keep their old w).
+__global__ void __launch_bounds__(TMA_THREADS, 2)
+update_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const double2 *__restrict__ h,
+                  float2 *__restrict__ w, double *__restrict__ nrm_partials, const double *gate,
+                  double *__restrict__ nrm2, double *__restrict__ counter, unsigned *__restrict__ ticket,
+                  double *err, unsigned wait_limit) {
+    if (gate != nullptr && !(gate[0] < 0.5 * gate[3])) return;     // DGKS: no second pass needed
+    constexpr int NW = DF_THREADS / 32;
+    constexpr int U = TMA_CHUNK / 2;
+    constexpr int UPT = U / DF_THREADS;
+    extern __shared__ __align__(128) float4 ring[];
+    __shared__ __align__(8) uint64_t full[TMA_SLOTS], empty[TMA_SLOTS];
+    __shared__ float4 hs[DST_MAX_VEC];
+    __shared__ double red[NW];
+    __shared__ float h1_sh;
+    __shared__ int failed, s_issued, s_done[NW];
+    volatile int *vfailed = &failed;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int64_t b, e;
+    df_slice2(n, b, e);
+    const int64_t len = e > b ? e - b : 0;
+    const int nch = (int)((len + TMA_CHUNK - 1) / TMA_CHUNK);
+    const int K = nch * nvec;
+    for (int j = tid; j < nvec; j += TMA_THREADS) {
+        const double2 c = h[j];
+        const float rh = (float)c.x, ih = (float)c.y;
+        hs[j] = make_float4(rh, (float)(c.x - (double)rh), ih, (float)(c.y - (double)ih));
+    }
+    if (warp == 0) {
+        double t = 0.0;
+        for (int j = lane; j < nvec; j += 32) t += fabs(h[j].x) + fabs(h[j].y);
+        t = dwarp_sum(t);
+        if (lane == 0) h1_sh = (float)t;
+    }
+    if (tid == 0) {
+        for (int q = 0; q < TMA_SLOTS; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], NW);
+        }
+        failed = 0;
+        s_issued = 0;
+        for (int q = 0; q < NW; ++q) s_done[q] = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    DfAcc nr;
+    nr.zero();
+    if (warp == NW) {
+        if (lane == 0) {
+            int pc = 0, pq = 0, k = 0;
+            for (; k < K && !*vfailed; ++k) {
+                const int slot = k % TMA_SLOTS;
+                if (k >= TMA_SLOTS &&
+                    !mbar_wait_bounded(&empty[slot], (unsigned)(((k / TMA_SLOTS) - 1) & 1), wait_limit)) {
+                    *vfailed = 1;
+                    break;
+                }
+                const int64_t c0 = b + (int64_t)pc * TMA_CHUNK;
+                const int64_t cnt = e - c0 < TMA_CHUNK ? e - c0 : TMA_CHUNK;
+                const unsigned bytes = (unsigned)(cnt * (int64_t)sizeof(float2));
+                mbar_arrive_expect_tx(&full[slot], bytes);
+                bulk_g2s(ring + (size_t)slot * U, V + (int64_t)pq * n + c0, bytes, &full[slot]);
+                if (++pq == nvec) { pq = 0; ++pc; }
+            }
+            s_issued = k;
+        }
+    } else {
+        int k = 0;
+        auto wait_item = [&]() -> const float4 * {
+            const int slot = k % TMA_SLOTS;
+            bool ok = __shfl_sync(0xffffffffu, *vfailed == 0 ? 1 : 0, 0) != 0;
+            if (ok) ok = mbar_wait_bounded(&full[slot], (unsigned)((k / TMA_SLOTS) & 1), wait_limit);
+            ok = __all_sync(0xffffffffu, ok) != 0;
+            if (!ok) {
+                if (lane == 0) *vfailed = 1;
+                return nullptr;
+            }
+            return (const float4 *)(ring + (size_t)slot * U);
+        };
+        auto release_item = [&]() {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[k % TMA_SLOTS]);
+            ++k;
+        };
+        const float h1 = h1_sh;
+        float4 *w4 = reinterpret_cast<float4 *>(w);
+        bool stop = false;
+        for (int c = 0; c < nch && !stop; ++c) {
+            const int64_t c0 = b + (int64_t)c * TMA_CHUNK;
+            const int units = (int)(((e - c0 < TMA_CHUNK) ? e - c0 : TMA_CHUNK) >> 1);
+            const int64_t g0 = c0 >> 1;                  // the chunk's first float4 of w
+            float sg[UPT];
+            AnAcc acc[UPT][4];
+#pragma unroll
+            for (int i = 0; i < UPT; ++i) {
+                const int u = tid + i * DF_THREADS;
+                const float4 a = u < units ? w4[g0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+                sg[i] = anchor_above(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))) + h1);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i][q].init(sg[i]);
+                acc[i][0].add(a.x); acc[i][1].add(a.y); acc[i][2].add(a.z); acc[i][3].add(a.w);
+            }
+            for (int j = 0; j < nvec; ++j) {
+                const float4 *sv = wait_item();
+                if (!sv) { stop = true; break; }
+                const float4 cj = hs[j];
+#pragma unroll
+                for (int i = 0; i < UPT; ++i) {
+                    const int u = tid + i * DF_THREADS;
+                    if (u < units) {
+                        const float4 v = sv[u];
+                        caxpy_an(v.x, v.y, cj, acc[i][0], acc[i][1]);
+                        caxpy_an(v.z, v.w, cj, acc[i][2], acc[i][3]);
+                    }
+                }
+                release_item();
+            }
+            if (stop) break;
+#pragma unroll
+            for (int i = 0; i < UPT; ++i) {
+                const int u = tid + i * DF_THREADS;
+                if (u >= units) continue;
+                const float4 o = make_float4((acc[i][0].hi - sg[i]) + acc[i][0].lo, (acc[i][1].hi - sg[i]) + acc[i][1].lo,
+                                             (acc[i][2].hi - sg[i]) + acc[i][2].lo, (acc[i][3].hi - sg[i]) + acc[i][3].lo);
+                w4[g0 + u] = o;
+                float p, r;
+                p = o.x * o.x; r = fmaf(o.x, o.x, -p); nr.add(p, r);
+                p = o.y * o.y; r = fmaf(o.y, o.y, -p); nr.add(p, r);
+                p = o.z * o.z; r = fmaf(o.z, o.z, -p); nr.add(p, r);
+                p = o.w * o.w; r = fmaf(o.w, o.w, -p); nr.add(p, r);
+            }
+        }
+        if (lane == 0) s_done[warp] = k;
+    }
+    __syncthreads();
+    if (tid == 0 && *vfailed) {
+        int lo = s_done[0];
+        for (int q = 1; q < NW; ++q) lo = s_done[q] < lo ? s_done[q] : lo;
+        for (int q = lo; q < s_issued; ++q)
+            mbar_wait_bounded(&full[q % TMA_SLOTS], (unsigned)((q / TMA_SLOTS) & 1), TMA_WAIT_LIMIT);
+    }
+    __syncthreads();
+    const double s_ = warp < NW ? dfwarp_sum(nr) : 0.0;
+    if (lane == 0 && warp < NW) red[warp] = s_;
+    __syncthreads();
+    if (*vfailed && tid == 0 && err) *err = 1.0;
+    if (!nrm_partials) return;
+    if (tid == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) t += red[q];
+        nrm_partials[blockIdx.x] = t;
+    }
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last || tid >= 32) return;
+    __threadfence();
+    double t = 0.0;
+    for (unsigned q = tid; q < gridDim.x; q += 32) t += __ldcg(nrm_partials + q);
+    t = dwarp_sum(t);
+    if (tid == 0) {
+        *nrm2 = t;
+        if (counter) *counter += 1.0;
+        *ticket = 0u;
+    }
+}
+
 // w <- w - sum_j V_j h_j for an FP32-stored unit-norm basis and FP32 w (h in
 // FP64, split per CTA), rounded to FP32 once; partials of ||w||^2 of the
 // stored result.  Per entry the bound is |w component| + sum_j |h_j|_1.
@@ -863,6 +1041,24 @@ int dst_k_project_tma(int64_t n, int nvec, const float2 *V, const float2 *w, dou
     return DST_OK;
 }
 
+int dst_k_update_tma(int64_t n, int nvec, const float2 *V, const double2 *h, float2 *w, double *nrm2,
+                     double *partials, int nblk, cudaStream_t s, const double *gate, double *counter,
+                     unsigned *ticket, double *err) {
+    if (n & 1) return DST_ERR_ARG;
+    static bool configured[64] = {};
+    int dev = 0;
+    DST_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        DST_CUDA_TRY(cudaFuncSetAttribute(update_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM));
+        if (dev >= 0 && dev < 64) configured[dev] = true;
+    }
+    double *pp = nrm2 ? partials : nullptr;
+    update_tma_kernel<<<nblk, TMA_THREADS, TMA_SMEM, s>>>(n, nvec, V, h, w, pp, gate, nrm2, counter, ticket, err,
+                                                          dst_internal_wait_limit(TMA_WAIT_LIMIT));
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
 int dst_k_update_df(int64_t n, int nvec, const float2 *V, const double2 *h, float2 *w, bool w_hi_only, double *nrm2,
                     double *partials, int nblk, cudaStream_t s, const double *gate, double *counter,
                     unsigned *ticket, bool vlo) {
@@ -910,15 +1106,16 @@ int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double
 
 extern "C" int dst_testing_fp32_arnoldi(int mode, int64_t n, int nvec, const void *V, void *w, void *h, void *nrm2,
                                         void *stream) {
-    if (mode < 0 || mode > 2 || n < 2 || (n & 1) || nvec < 1 || nvec > DST_MAX_VEC || !V || !w || !h ||
-        (mode == 2 && !nrm2)) {
+    if (mode < 0 || mode > 3 || n < 2 || (n & 1) || nvec < 1 || nvec > DST_MAX_VEC || !V || !w || !h ||
+        (mode >= 2 && !nrm2)) {
         dst_internal_set_error_detail("dst_testing_fp32_arnoldi: bad mode, size (n even >= 2, 1 <= nvec <= 64) "
                                       "or pointer");
         return DST_ERR_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int nblk_reg = std::min(dst_reduction_blocks(n), 3 * 152);
-    const int nblk = mode == 1 ? dst_tma_projection_blocks(n) : (mode == 2 ? dst_reduction_blocks(n) : nblk_reg);
+    const int nblk = (mode == 1 || mode == 3) ? dst_tma_projection_blocks(n)
+                                              : (mode == 2 ? dst_reduction_blocks(n) : nblk_reg);
     const size_t pbytes = sizeof(double2) * (size_t)nblk * (nvec + 1);
     char *scr = nullptr;
     if (cudaMallocAsync((void **)&scr, pbytes + 256 + 256, s) != cudaSuccess) {
@@ -937,18 +1134,21 @@ extern "C" int dst_testing_fp32_arnoldi(int mode, int64_t n, int nvec, const voi
         else if (mode == 1)
             rc = dst_k_project_tma(n, nvec, (const float2 *)V, (const float2 *)w, (double2 *)h, partials, nblk, s,
                                    nullptr, nullptr, ticket, err);
-        else
+        else if (mode == 2)
             rc = dst_k_update_df(n, nvec, (const float2 *)V, (const double2 *)h, (float2 *)w, true, (double *)nrm2,
                                  (double *)partials, nblk, s, nullptr, nullptr, ticket + 1, false);
+        else
+            rc = dst_k_update_tma(n, nvec, (const float2 *)V, (const double2 *)h, (float2 *)w, (double *)nrm2,
+                                  (double *)partials, nblk, s, nullptr, nullptr, ticket + 1, err);
     }
     double e = 0.0;
-    if (rc == DST_OK && mode == 1 &&
+    if (rc == DST_OK && (mode == 1 || mode == 3) &&
         (cudaMemcpyAsync(&e, err, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
          cudaStreamSynchronize(s) != cudaSuccess))
         rc = DST_ERR_CUDA;
     cudaFreeAsync(scr, s);
     if (rc == DST_OK && e != 0.0) {
-        dst_internal_set_error_detail("dst_testing_fp32_arnoldi: a bulk-copy wait of the projection timed out");
+        dst_internal_set_error_detail("dst_testing_fp32_arnoldi: a bulk-copy wait timed out");
         rc = DST_ERR_CUDA;
     }
     return rc;

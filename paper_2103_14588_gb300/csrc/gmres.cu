@@ -56,7 +56,7 @@ struct Workspace {
 // One Arnoldi step's record in Workspace::cols: first-pass coefficients
 // (DST_MAX_VEC complex), second-pass coefficients (DST_MAX_VEC complex), and
 // 8 doubles: [0] ||w||^2 after the last pass, [3] before the first update,
-// [6] 1 if the second pass ran, [7] 1 if a bulk-copy wait of the projection timed out.
+// [6] 1 if the second pass ran, [7] 1 if a bulk-copy wait of the projection or update timed out.
 constexpr int COL_STRIDE = 4 * DST_MAX_VEC + 8;
 
 // FP32-stored bases of at least this many unknowns use the bulk-copy fed
@@ -578,7 +578,7 @@ struct Solver {
     // device) and the scaling, all on stream s.
     int enqueue_steps(int steps, bool vlo) {
         const int64_t n = w.n;
-        // large FP32-stored bases: the projection fed by bulk asynchronous copies
+        // large FP32-stored bases: the projection and the update fed by bulk asynchronous copies
         const bool use_tma = !vlo && n >= TMA_MIN_UNKNOWNS;
         const int nblk_tma = dst_tma_projection_blocks(n);
         const double dn = (double)n;
@@ -614,9 +614,12 @@ struct Solver {
                                                        w.partials_r, nullptr, w.tickets, vlo);
                  })))
                 return rc;
-            if ((rc = run(K_UPDATE, 1, vb * dn * nv + 8.0 * dn + vb * dn, 8.0 * dn * nv,
-                          [&] { return dst_k_update_df(n, nv, Vd, c1, wv, true, nr, w.partials_r, nblk, s,
-                                                       nullptr, nullptr, w.tickets + 1, vlo); })))
+            if ((rc = run(K_UPDATE, 1, vb * dn * nv + 8.0 * dn + vb * dn, 8.0 * dn * nv, [&] {
+                     return use_tma ? dst_k_update_tma(n, nv, Vd, c1, wv, nr, w.partials_r, nblk_tma, s, nullptr,
+                                                       nullptr, w.tickets + 1, nr + 7)
+                                    : dst_k_update_df(n, nv, Vd, c1, wv, true, nr, w.partials_r, nblk, s, nullptr,
+                                                      nullptr, w.tickets + 1, vlo);
+                 })))
                 return rc;
             // second pass, gated on the device by the DGKS test unless always on
             // (CGS2) or never (ortho 2: the record's second-pass slots stay zero)
@@ -629,9 +632,12 @@ struct Solver {
                                                        nullptr, gate, w.tickets, vlo);
                  })))
                 return rc;
-            if (ortho != 2 && (rc = run(K_UPDATE, 1, g2 * vb * dn * (nv + 2), g2 * 8.0 * dn * nv,
-                                        [&] { return dst_k_update_df(n, nv, Vd, c2, wv, !vlo, nr, w.partials_r, nblk,
-                                                                     s, gate, nr + 6, w.tickets + 1, vlo); })))
+            if (ortho != 2 && (rc = run(K_UPDATE, 1, g2 * vb * dn * (nv + 2), g2 * 8.0 * dn * nv, [&] {
+                     return use_tma ? dst_k_update_tma(n, nv, Vd, c2, wv, nr, w.partials_r, nblk_tma, s, gate, nr + 6,
+                                                       w.tickets + 1, nr + 7)
+                                    : dst_k_update_df(n, nv, Vd, c2, wv, !vlo, nr, w.partials_r, nblk, s, gate,
+                                                      nr + 6, w.tickets + 1, vlo);
+                 })))
                 return rc;
             if ((rc = run(K_SCALE, 1, 2.0 * vb * dn, 6.0 * dn, [&] { return dst_k_scale_df(n, wv, nr, s, vlo); })))
                 return rc;
@@ -698,7 +704,7 @@ struct Solver {
             const double *c1 = w.host_cols + (size_t)j * COL_STRIDE;
             const double *nr = c1 + 4 * DST_MAX_VEC;
             if (nr[7] != 0.0) {
-                dst_internal_set_error_detail("dst_solve: a bulk-copy wait of the projection timed out");
+                dst_internal_set_error_detail("dst_solve: a bulk-copy wait of the Gram-Schmidt timed out");
                 return DST_ERR_CUDA;
             }
             if (nr[6] > 0.0) {

@@ -73,3 +73,27 @@ def test_update_error_bound(n, nvec):
     assert torch.all((got - exact).abs() <= 1.5 * half_ulp + 2.0 ** -36 * bound)
     stored = float((got.abs() ** 2).sum())
     assert abs(float(nrm2[0]) - stored) <= 1e-10 * stored
+
+
+@pytest.mark.parametrize("n,nvec", [(4063232, 9), (6 * 2048 + 2, 3), (4063232, 30)])
+def test_bulk_copy_update_equals_register_update(n, nvec):
+    """The update fed by bulk copies (mode 3, the solver's from 4M unknowns) does the
+    register-fed update's arithmetic per entry: the same stored w bit for bit, and
+    the same ||w||^2 up to the order of the FP64 partial sums."""
+    import torch
+    from paper_2103_14588_gb300 import binding as B
+    lib = B.library()
+    gen = torch.Generator(device="cuda").manual_seed(5 * n + nvec)
+    V = torch.randn(nvec, n, dtype=torch.complex128, device="cuda", generator=gen)
+    V = (V / torch.linalg.vector_norm(V, dim=1, keepdim=True)).to(torch.complex64).contiguous()
+    w = torch.randn(n, dtype=torch.complex128, device="cuda", generator=gen).to(torch.complex64)
+    h = torch.randn(nvec, dtype=torch.complex128, device="cuda", generator=gen) * 1e-3 * np.sqrt(n)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    w_reg, w_tma = w.clone(), w.clone()
+    n_reg = torch.zeros(1, dtype=torch.float64, device="cuda")
+    n_tma = torch.zeros(1, dtype=torch.float64, device="cuda")
+    assert lib.dst_testing_fp32_arnoldi(2, n, nvec, _ptr(V), _ptr(w_reg), _ptr(h), _ptr(n_reg), st) == 0
+    assert lib.dst_testing_fp32_arnoldi(3, n, nvec, _ptr(V), _ptr(w_tma), _ptr(h), _ptr(n_tma), st) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(w_tma, w_reg)
+    assert abs(float(n_tma[0]) - float(n_reg[0])) <= 1e-13 * float(n_reg[0])
