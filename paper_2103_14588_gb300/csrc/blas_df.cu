@@ -921,7 +921,7 @@ __global__ void scale_df_kernel(int64_t n, float2 *__restrict__ v, const double 
 
 // v <- v / sqrt(*nrm2) for an FP32-stored vector (the same compensated
 // product as scale_df_kernel<false>, rounded once), two entries per 16-byte
-// access and a few CTAs per SM, each computing the FP64 factor once.
+// access, up to eight CTAs per SM, each computing the FP64 factor once.
 __global__ void __launch_bounds__(256) scale_f32_kernel(int64_t n, float2 *__restrict__ v,
                                                         const double *__restrict__ nrm2) {
     __shared__ float s_sh[2];
@@ -939,7 +939,17 @@ __global__ void __launch_bounds__(256) scale_f32_kernel(int64_t n, float2 *__res
         df_prod(a, 0.f, sh, sl, p, e);
         return p + e;
     };
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
+    // four independent 16-byte loads in flight per thread
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; u + 3 * T < nu; u += 4 * T) {
+        float4 a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = v4[u + k * T];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v4[u + k * T] = make_float4(sc(a[k].x), sc(a[k].y), sc(a[k].z), sc(a[k].w));
+    }
+    for (; u < nu; u += T) {
         const float4 a = v4[u];
         v4[u] = make_float4(sc(a.x), sc(a.y), sc(a.z), sc(a.w));
     }
@@ -1080,8 +1090,8 @@ int dst_k_scale_df(int64_t n, float2 *v, const double *nrm2, cudaStream_t s, boo
         scale_df_kernel<true><<<df_stream_blocks(n), 256, 0, s>>>(n, v, nrm2);
     } else {
         if (n & 1) return DST_ERR_ARG;          // two entries per 16-byte access
-        int64_t b = (n / 2 + 255) / 256;
-        if (b > 4 * 152) b = 4 * 152;
+        int64_t b = (n / 2 + 1023) / 1024;
+        if (b > 8 * 152) b = 8 * 152;
         scale_f32_kernel<<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(n, v, nrm2);
     }
     DST_CUDA_TRY(cudaGetLastError());
