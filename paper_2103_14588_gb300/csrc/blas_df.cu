@@ -375,13 +375,14 @@ project_f32_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
 // memory through a ring of TMA_SLOTS 16 KB bulk copies completed on mbarriers:
 // a producer warp keeps up to 96 KB per CTA in flight (two CTAs per SM),
 // independent of the arithmetic, in contiguous 16 KB transfers, refilling a
-// slot once all eight consumer warps have released it.  Each CTA owns a
-// contiguous slice of entries, cut into 2048-entry chunks; the copy sequence
-// is, per group of TMA_GROUP basis vectors and per chunk, the chunk of w and then
-// the chunks of the group's vectors (w is read once per group: reducing every
-// vector's chunk contribution over the warp instead, to read w once, made the
-// consumers the bottleneck; groups of eight read w a quarter as often as groups
-// of four for nvec = 30).  Each chunk's contribution is accumulated in the
+// slot once all eight consumer warps have released it.  Each CTA owns one group
+// of TMA_GROUP basis vectors over a contiguous slice of entries, cut into
+// 2048-entry chunks; the copy sequence is, per chunk, the chunk of w and then
+// the chunks of the group's vectors.  The CTAs of the groups of one slice are
+// consecutive in the grid and run at the same time, so each chunk of w comes
+// from HBM once and from L2 for the other groups (reducing every vector's chunk
+// contribution over the warp instead, to read w once in one CTA, made the
+// consumers the bottleneck).  Each chunk's contribution is accumulated in the
 // anchored scheme with a bound taken from that chunk of w, then folded into a
 // df32 per-thread sum.
 constexpr int TMA_CHUNK = 2048;                 // entries per copy (16 KB)
@@ -417,16 +418,28 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
     constexpr int UPT = U / DF_THREADS;              // units per consumer thread per chunk
     extern __shared__ __align__(128) float4 ring[];  // TMA_SLOTS x U
     __shared__ __align__(8) uint64_t full[TMA_SLOTS], empty[TMA_SLOTS];
-    __shared__ double red[NW][2 * DST_MAX_VEC + 1];
+    __shared__ double red[NW][2 * TMA_GROUP + 1];
     __shared__ int failed, s_issued, s_done[NW];
     volatile int *vfailed = &failed;                 // polled across warps
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // CTA = (slice, group): the ngr CTAs of a slice are consecutive, so they stream the
+    // slice's chunks of w at the same time and all but one read them from L2
+    const int ngr = (nvec + TMA_GROUP - 1) / TMA_GROUP;
+    const int nsl = (int)gridDim.x / ngr;
+    const int slice = (int)blockIdx.x / ngr, grp = (int)blockIdx.x % ngr;
+    // groups as even as possible (sizes differ by one at most), so that the CTAs of a
+    // slice move through its chunks at the same pace
+    const int j0 = grp * nvec / ngr, gv = (grp + 1) * nvec / ngr - j0;
     int64_t b, e;
-    df_slice2(n, b, e);
+    {
+        int64_t per = (n + nsl - 1) / nsl;
+        per += per & 1;
+        b = (int64_t)slice * per;
+        e = b + per < n ? b + per : n;
+    }
     const int64_t len = e > b ? e - b : 0;
     const int nch = (int)((len + TMA_CHUNK - 1) / TMA_CHUNK);
-    const int ngr = (nvec + TMA_GROUP - 1) / TMA_GROUP;
-    const int K = nch * (ngr + nvec);                // copies this CTA consumes
+    const int K = nch * (1 + gv);                    // copies this CTA consumes
     if (tid == 0) {
         for (int q = 0; q < TMA_SLOTS; ++q) {
             mbar_init(&full[q], 1);                  // the producer's arrival + the copy's bytes
@@ -444,7 +457,7 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
         // producer warp: lane 0 issues the copies in consumption order, refilling a
         // slot once every consumer warp has released it
         if (lane == 0) {
-            int pg = 0, pc = 0, pq = 0, k = 0;
+            int pc = 0, pq = 0, k = 0;
             for (; k < K && !*vfailed; ++k) {
                 const int slot = k % TMA_SLOTS;
                 if (k >= TMA_SLOTS &&
@@ -452,17 +465,13 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
                     *vfailed = 1;
                     break;
                 }
-                const int gv = nvec - TMA_GROUP * pg < TMA_GROUP ? nvec - TMA_GROUP * pg : TMA_GROUP;
                 const int64_t c0 = b + (int64_t)pc * TMA_CHUNK;
                 const int64_t cnt = e - c0 < TMA_CHUNK ? e - c0 : TMA_CHUNK;
-                const float2 *src = pq == 0 ? w + c0 : V + (int64_t)(TMA_GROUP * pg + pq - 1) * n + c0;
+                const float2 *src = pq == 0 ? w + c0 : V + (int64_t)(j0 + pq - 1) * n + c0;
                 const unsigned bytes = (unsigned)(cnt * (int64_t)sizeof(float2));
                 mbar_arrive_expect_tx(&full[slot], bytes);
                 bulk_g2s(ring + (size_t)slot * U, src, bytes, &full[slot]);
-                if (++pq > gv) {
-                    pq = 0;
-                    if (++pc == nch) { pc = 0; ++pg; }
-                }
+                if (++pq > gv) { pq = 0; ++pc; }
             }
             s_issued = k;
         }
@@ -486,8 +495,8 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
             ++k;
         };
         bool stop = false;
-        for (int g = 0; g < ngr && !stop; ++g) {
-            const int gv = nvec - TMA_GROUP * g < TMA_GROUP ? nvec - TMA_GROUP * g : TMA_GROUP;
+        {
+            const int g = grp;
             DfAcc R[TMA_GROUP], I[TMA_GROUP];
 #pragma unroll
             for (int q = 0; q < TMA_GROUP; ++q) { R[q].zero(); I[q].zero(); }
@@ -504,7 +513,7 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
                         const int u = tid + i * DF_THREADS;
                         a[i] = u < units ? sw4[u] : make_float4(0.f, 0.f, 0.f, 0.f);
                         bound += (fabsf(a[i].x) + fabsf(a[i].y)) + (fabsf(a[i].z) + fabsf(a[i].w));
-                        if (g == 0) {
+                        if (g == 0) {                    // ||w||^2: the first group's CTA of the slice
                             float p, r;
                             p = a[i].x * a[i].x; r = fmaf(a[i].x, a[i].x, -p); wn.add(p, r);
                             p = a[i].y * a[i].y; r = fmaf(a[i].y, a[i].y, -p); wn.add(p, r);
@@ -515,7 +524,9 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
                     release_item();
                 }
                 const float sigma = anchor_above(bound);
-                for (int q = 0; q < gv; ++q) {
+#pragma unroll
+                for (int q = 0; q < TMA_GROUP; ++q) {
+                    if (q >= gv) break;
                     const float4 *sv = wait_item();
                     if (!sv) { stop = true; break; }
                     AnAcc re, im;
@@ -535,14 +546,13 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
                     release_item();
                 }
             }
-            if (stop) break;
 #pragma unroll
             for (int q = 0; q < TMA_GROUP; ++q) {
-                if (q < gv) {
+                if (q < gv && !stop) {
                     const double sr = dfwarp_sum(R[q]), si = dfwarp_sum(I[q]);
                     if (lane == 0) {
-                        red[warp][2 * (TMA_GROUP * g + q)] = sr;
-                        red[warp][2 * (TMA_GROUP * g + q) + 1] = si;
+                        red[warp][2 * q] = sr;
+                        red[warp][2 * q + 1] = si;
                     }
                 }
             }
@@ -561,22 +571,23 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
     // every issued copy was waited for by the consumers (or the producer stopped
     // issuing after a failed wait); the ring is idle here
     const double wsum = warp < NW ? dfwarp_sum(wn) : 0.0;
-    if (lane == 0 && warp < NW) red[warp][2 * DST_MAX_VEC] = wsum;
+    if (lane == 0 && warp < NW) red[warp][2 * TMA_GROUP] = wsum;
     __syncthreads();
     if (*vfailed && tid == 0 && err) *err = 1.0;
-    for (int q = tid; q < 2 * nvec; q += TMA_THREADS) {
+    // partials [slice][nvec]: this CTA's group of coefficients of its slice
+    for (int q = tid; q < 2 * gv; q += TMA_THREADS) {
         double s_ = 0.0;
 #pragma unroll
         for (int kk = 0; kk < NW; ++kk) s_ += red[kk][q];
-        reinterpret_cast<double *>(partials + (int64_t)blockIdx.x * nvec)[q] = s_;
+        reinterpret_cast<double *>(partials + (int64_t)slice * nvec + j0)[q] = s_;
     }
-    // ||w||^2 partial of this CTA goes after the coefficient partials of all CTAs
-    double *wparts = reinterpret_cast<double *>(partials + (int64_t)gridDim.x * nvec);
-    if (tid == 0) {
+    // ||w||^2 partial of the slice goes after the coefficient partials of all slices
+    double *wparts = reinterpret_cast<double *>(partials + (int64_t)nsl * nvec);
+    if (tid == 0 && grp == 0) {
         double s_ = 0.0;
 #pragma unroll
-        for (int kk = 0; kk < NW; ++kk) s_ += red[kk][2 * DST_MAX_VEC];
-        wparts[blockIdx.x] = s_;
+        for (int kk = 0; kk < NW; ++kk) s_ += red[kk][2 * TMA_GROUP];
+        wparts[slice] = s_;
     }
     __shared__ bool last;
     __threadfence();
@@ -589,9 +600,9 @@ project_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const floa
     for (int q = warp; q < 2 * nvec + 1; q += NW) {
         double s_ = 0.0;
         if (q < 2 * nvec) {
-            for (unsigned kk = lane; kk < gridDim.x; kk += 32) s_ += __ldcg(pd + (size_t)kk * 2 * nvec + q);
+            for (int kk = lane; kk < nsl; kk += 32) s_ += __ldcg(pd + (size_t)kk * 2 * nvec + q);
         } else if (wnrm2) {
-            for (unsigned kk = lane; kk < gridDim.x; kk += 32) s_ += __ldcg(wparts + kk);
+            for (int kk = lane; kk < nsl; kk += 32) s_ += __ldcg(wparts + kk);
         }
         s_ = dwarp_sum(s_);
         if (lane == 0) {
@@ -1045,8 +1056,14 @@ int dst_k_project_tma(int64_t n, int nvec, const float2 *V, const float2 *w, dou
         DST_CUDA_TRY(cudaFuncSetAttribute(project_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM));
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
-    project_tma_kernel<<<nblk, TMA_THREADS, TMA_SMEM, s>>>(n, nvec, V, w, partials, gate, h, wnrm2, ticket, err,
-                                                           dst_internal_wait_limit(TMA_WAIT_LIMIT));
+    // nblk slices at most (the partials hold nblk x (nvec + 1)), one CTA per slice and group
+    // of TMA_GROUP basis vectors, one wave of two CTAs per SM
+    const int ngr = (nvec + TMA_GROUP - 1) / TMA_GROUP;
+    int nsl = 2 * 152 / ngr;
+    if (nsl > nblk) nsl = nblk;
+    if (nsl < 1) nsl = 1;
+    project_tma_kernel<<<nsl * ngr, TMA_THREADS, TMA_SMEM, s>>>(n, nvec, V, w, partials, gate, h, wnrm2, ticket, err,
+                                                                dst_internal_wait_limit(TMA_WAIT_LIMIT));
     DST_CUDA_TRY(cudaGetLastError());
     return DST_OK;
 }
