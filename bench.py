@@ -477,10 +477,11 @@ def run_batch_stated(torch, B, count, cap=4000):
 
 
 def run_precond_bench(torch, B):
-    """Flexible GMRES with the Crank-Nicolson sweep, and with the sweep plus the learned
-    U-Net correction (trained here on pairs generated on the GPU), against the plain
-    mixed solve, on the 2+1 Zitterbewegung packet at 48^3 (where the sweep preconditions)
-    and at the bench size 96^3 (where its quality is gone: ||A M v - v|| ~ ||v||)."""
+    """Flexible GMRES with the Crank-Nicolson sweep, with the sweep plus the learned
+    U-Net correction (trained here on pairs generated on the GPU) and with node-block
+    Jacobi, against the plain mixed solve, on the 2+1 Zitterbewegung packet at 48^3
+    (where the sweep preconditions) and at 96^3 (where its quality is gone:
+    ||A M v - v|| ~ ||v||)."""
     import numpy as _np
     out = {}
     base = {"restart": RESTART, "rtol": RTOL, "max_iters": 2000, "mixed_precision": 1, "inner_rtol": INNER_RTOL}
@@ -490,7 +491,8 @@ def run_precond_bench(torch, B):
         with B.Mesh.from_workload(w) as m:
             rec["unknowns"] = m.n_unknowns
             psi = torch.zeros(m.n_unknowns, dtype=torch.complex128, device="cuda")
-            runs = [("plain", dict(base, ortho=ORTHO)), ("cn_sweep", dict(base, precond=B.DST_PRECOND_CN_SWEEP))]
+            runs = [("plain", dict(base, ortho=ORTHO)), ("cn_sweep", dict(base, precond=B.DST_PRECOND_CN_SWEEP)),
+                    ("block_jacobi", dict(base, precond=B.DST_PRECOND_BLOCK_JACOBI))]
             net = None
             if n == 48:
                 net = B.UNet(m.handle)

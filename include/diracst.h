@@ -416,13 +416,28 @@ DST_API int dst_testing_fp32_arnoldi(int mode, int64_t n, int nvec, const void *
  * FP32 (the precision of the inner solve), the layer-solve factors in FP64
  * rounded to FP32.  Takes stream-ordered scratch of about one FP32 vector (plus
  * the factors, 32 NC^2 bytes per x node and frequency, on Dirichlet-x meshes).
- * kind DST_PRECOND_CN_SWEEP, or DST_PRECOND_CN_LEARNED (the sweep plus the
+ * kind DST_PRECOND_CN_SWEEP, DST_PRECOND_CN_LEARNED (the sweep plus the
  * learned correction below, with the network attached to the mesh by
- * dst_set_learned_precond; two more FP32 vectors of scratch).
+ * dst_set_learned_precond; two more FP32 vectors of scratch), or
+ * DST_PRECOND_BLOCK_JACOBI:
+ *   DST_PRECOND_BLOCK_JACOBI  z = blockdiag(A_nn)^-1 v, A_nn the NC x NC block of
+ *     D_w22 coupling the components of unknown node n with themselves: the
+ *     classical comparator.  Any mesh.  The blocks are read off the operator by
+ *     probing (colours of nodes two steps apart along some axis, one FP32 apply
+ *     per colour and component, 3^(d+1) x NC applies on meshes whose periodic
+ *     lengths are multiples of 3), inverted in FP64 and kept in FP32 by the mesh
+ *     (NC^2 complex FP32 per node) until its mass or potential changes; a
+ *     singular block is replaced by the identity.  The first use synchronises.
  * Errors: DST_ERR_ARG (kind, mesh not covered, no network attached),
  * DST_ERR_OOM, DST_ERR_CUDA.
  */
-enum { DST_PRECOND_NONE = 0, DST_PRECOND_CN_SWEEP = 1, DST_PRECOND_CN_SWEEP2 = 2, DST_PRECOND_CN_LEARNED = 3 };
+enum {
+    DST_PRECOND_NONE = 0,
+    DST_PRECOND_CN_SWEEP = 1,
+    DST_PRECOND_CN_SWEEP2 = 2,
+    DST_PRECOND_CN_LEARNED = 3,
+    DST_PRECOND_BLOCK_JACOBI = 4
+};
 DST_API int dst_precond_apply(const dst_mesh *mesh, int kind, const void *v, void *z, void *stream);
 
 /*

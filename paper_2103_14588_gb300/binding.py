@@ -21,7 +21,7 @@ DST_ERR_ARG, DST_ERR_OOM, DST_ERR_CUDA, DST_ERR_NAN, DST_ERR_STATE = -1, -2, -3,
 DST_BC_PERIODIC, DST_BC_OPEN, DST_BC_DIRICHLET = 0, 1, 2
 DST_FP64, DST_FP32 = 0, 1
 DST_TEST_WAIT_LIMIT, DST_TEST_FAIL_ALLOC = 1, 2
-DST_PRECOND_NONE, DST_PRECOND_CN_SWEEP, DST_PRECOND_CN_SWEEP2, DST_PRECOND_CN_LEARNED = 0, 1, 2, 3
+DST_PRECOND_NONE, DST_PRECOND_CN_SWEEP, DST_PRECOND_CN_SWEEP2, DST_PRECOND_CN_LEARNED, DST_PRECOND_BLOCK_JACOBI = 0, 1, 2, 3, 4
 
 EXPORTED = (
     "dst_create_mesh", "dst_destroy_mesh", "dst_mesh_sizes", "dst_set_mass", "dst_set_potential",

@@ -86,7 +86,8 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w, int precond
     const size_t opr = take(sizeof(double) * (size_t)nblk);
     const size_t ocols = take(sizeof(double) * (size_t)COL_STRIDE * DST_MAX_VEC);
     const size_t oZ = precond ? take(sizeof(float2) * (size_t)n * m) : 0;
-    const size_t opres = precond >= DST_PRECOND_CN_SWEEP2 ? take(sizeof(float2) * (size_t)n) : 0;
+    const bool need_pr = precond == DST_PRECOND_CN_SWEEP2 || precond == DST_PRECOND_CN_LEARNED;
+    const size_t opres = need_pr ? take(sizeof(float2) * (size_t)n) : 0;
     const size_t opz2 = precond == DST_PRECOND_CN_SWEEP2 ? take(sizeof(float2) * (size_t)n) : 0;
     const size_t osw = precond ? take(sweep_bytes) : 0;
     const size_t total = off;
@@ -126,7 +127,7 @@ int setup_workspace(dst_mesh *mesh, int m, bool mixed, Workspace &w, int precond
     w.partials_r = (double *)(base + opr);
     w.cols = (double *)(base + ocols);
     w.Z = precond ? (float2 *)(base + oZ) : nullptr;
-    w.pr = precond >= DST_PRECOND_CN_SWEEP2 ? (float2 *)(base + opres) : nullptr;
+    w.pr = need_pr ? (float2 *)(base + opres) : nullptr;
     w.pz2 = precond == DST_PRECOND_CN_SWEEP2 ? (float2 *)(base + opz2) : nullptr;
     w.sweep_scratch = precond ? (void *)(base + osw) : nullptr;
     return DST_OK;
@@ -552,6 +553,9 @@ struct Solver {
     int precondition(const float2 *v, float2 *z, float2 *tmp) {
         const int64_t n = w.n;
         const double dn = (double)n;
+        if (precond == DST_PRECOND_BLOCK_JACOBI)       // z = blockdiag(A_nn)^-1 v
+            return run(K_PRECOND, 1, (16.0 + 8.0 * mesh->nc) * dn, 8.0 * mesh->nc * dn,
+                       [&] { return dst_internal_jacobi_apply(mesh, v, z, s); });
         const double sweep_bytes = (plan.has_fft ? 48.0 : 40.0) * dn + (double)plan.table_bytes * plan.g.nt;
         int rc = run(K_PRECOND, plan.has_fft ? 4 : 3, sweep_bytes, 0.0,
                      [&] { return dst_sweep_apply(plan, n, v, z, s); });
@@ -865,7 +869,8 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     sv.ortho = o.ortho;
     sv.precond = o.precond;
     size_t sweep_bytes = 0;
-    if (o.precond) {
+    const bool sweep = o.precond && o.precond != DST_PRECOND_BLOCK_JACOBI;
+    if (sweep) {
         int rp = dst_sweep_plan(mesh, sv.plan);
         if (rp) return rp;
         sweep_bytes = dst_sweep_scratch_bytes(sv.plan, mesh->n_unknowns);
@@ -873,7 +878,8 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     int rc = setup_workspace(mesh, o.method == 1 ? std::max(o.restart, 5) : o.restart, mixed, sv.w, o.precond,
                              sweep_bytes);
     if (rc) return rc;
-    if (o.precond && (rc = dst_sweep_setup(mesh, sv.plan, sv.w.sweep_scratch, s))) return rc;
+    if (sweep && (rc = dst_sweep_setup(mesh, sv.plan, sv.w.sweep_scratch, s))) return rc;
+    if (o.precond == DST_PRECOND_BLOCK_JACOBI && (rc = dst_internal_jacobi_setup(mesh, s))) return rc;
     // the mesh owns its page-locked record buffer (freed with the mesh), so
     // solves from short-lived threads leave no pinned memory behind
     if (!mesh->host_pinned) {
@@ -1001,7 +1007,7 @@ extern "C" int dst_solve(dst_mesh *mesh, const dst_solve_opts *opts, void *psi, 
     if (!mesh || !psi || o.restart < 1 || o.restart > DST_MAX_VEC - 1 || o.max_iters < 0 || !(o.rtol >= 0) ||
         (o.mixed_precision && (!(o.inner_rtol > 0) || o.max_refine < 1)) || o.ortho < 0 || o.ortho > 2 ||
         o.mixed_ortho < 0 || o.mixed_ortho > 2 || o.inner_cycles < 0 || o.method < 0 || o.method > 1 ||
-        (o.method == 1 && o.mixed_precision) || o.precond < 0 || o.precond > DST_PRECOND_CN_LEARNED ||
+        (o.method == 1 && o.mixed_precision) || o.precond < 0 || o.precond > DST_PRECOND_BLOCK_JACOBI ||
         (o.precond == DST_PRECOND_CN_LEARNED && !dst_internal_unet_fits(mesh->unet, mesh)) ||
         (o.precond && (!o.mixed_precision || o.mixed_ortho != 2 || o.method != 0))) {
         rc = DST_ERR_ARG;

@@ -87,7 +87,16 @@ struct dst_mesh {
     size_t ws_bytes;
     double *host_pinned;          // page-locked host copy of the per-step records (lazily, by dst_solve)
     dst_unet *unet;               // learned correction of the sweep preconditioner (not owned), or null
+    void *d_jac;                  // inverse node blocks of the block Jacobi preconditioner (float2
+                                  // [node][NC][NC]), built on first use
+    bool jac_valid;               // d_jac matches the current mass and potential
+    int64_t jac_singular;         // nodes whose block was singular (identity used there)
 };
+
+// Node-block Jacobi preconditioner (jacobi.cu): build the inverse blocks of the
+// current operator (once; synchronises s), and z = blockdiag(A_nn)^-1 v in FP32.
+int dst_internal_jacobi_setup(dst_mesh *mesh, cudaStream_t s);
+int dst_internal_jacobi_apply(const dst_mesh *mesh, const float2 *v, float2 *z, cudaStream_t s);
 
 // The learned correction (unet.cu): z += alpha U(rho / ||rho||) with alpha the
 // complex least-squares scale minimising ||rho - alpha A U|| (tmp: a free FP32

@@ -250,6 +250,9 @@ extern "C" int dst_create_mesh(int d, const int64_t n_el[4], const double lo[4],
     m->d_psi0 = nullptr;
     m->d_bd = nullptr;
     m->unet = nullptr;
+    m->d_jac = nullptr;
+    m->jac_valid = false;
+    m->jac_singular = 0;
     m->ws = nullptr;
     m->host_pinned = nullptr;
     m->tile_variant[0] = m->tile_variant[1] = 0;
@@ -277,6 +280,7 @@ extern "C" int dst_destroy_mesh(dst_mesh *mesh) {
     cudaFree(mesh->d_V);
     cudaFree(mesh->d_psi0);
     cudaFree(mesh->d_bd);
+    cudaFree(mesh->d_jac);
     cudaFree(mesh->ws);
     if (mesh->host_pinned) cudaFreeHost(mesh->host_pinned);
     cudaSetDevice(dev_prev);
@@ -297,7 +301,10 @@ extern "C" int dst_set_mass(dst_mesh *mesh, double m) {
     std::vector<double> w;
     int rc = build_weights(mesh, m, mesh->V, w);
     if (rc == DST_OK) rc = upload_weights(mesh, w);
-    if (rc == DST_OK) mesh->m = m;
+    if (rc == DST_OK) {
+        mesh->m = m;
+        mesh->jac_valid = false;      // the Jacobi blocks depend on the operator
+    }
     return rc;
 }
 
@@ -333,6 +340,7 @@ static int set_potential(dst_mesh *mesh, const double *V_elem) {
     if ((rc = upload_weights(mesh, w)) != DST_OK) return rc;
     mesh->V.swap(V);
     mesh->v_general = general;
+    mesh->jac_valid = false;
     return DST_OK;
 }
 

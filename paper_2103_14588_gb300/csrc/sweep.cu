@@ -661,6 +661,11 @@ int dst_sweep_apply(const SweepPlan &p, int64_t n_unknowns, const float2 *v, flo
 
 extern "C" int dst_precond_apply(const dst_mesh *mesh, int kind, const void *v, void *z, void *stream) {
     if (!mesh || !v || !z || v == z) return DST_ERR_ARG;
+    if (kind == DST_PRECOND_BLOCK_JACOBI) {
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = dst_internal_jacobi_setup(const_cast<dst_mesh *>(mesh), s);
+        return rc ? rc : dst_internal_jacobi_apply(mesh, (const float2 *)v, (float2 *)z, s);
+    }
     if (kind != DST_PRECOND_CN_SWEEP && kind != DST_PRECOND_CN_LEARNED) {
         dst_internal_set_error_detail("dst_precond_apply: unknown preconditioner kind");
         return DST_ERR_ARG;
