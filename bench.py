@@ -60,9 +60,10 @@ FP64_FLOP_PER_CLK_SM = 4.0     # 2 FP64 FMA per clock per SM (1/64 of the FP32 r
 FP64_PROBE_TFLOPS = 1.196      # FP64 FMA throughput measured by a probe kernel on this machine
 CLASSES = ("apply64", "apply32", "cast", "project", "update", "scale", "misc", "rhs", "precond")
 # DRAM read+write bytes per algorithmic byte of a kernel class, from one ncu capture of
-# its kernel as committed (profiles/gram_schmidt_klein_3p1_32.md: update_tma_kernel at
-# 4.06M unknowns, nv = 11); classes without a capture of the current kernel are absent.
-TRAFFIC_RATIO = {"update": 0.983}
+# its kernel as committed (profiles/gram_schmidt_klein_3p1_32.md: update_tma_kernel and
+# project_tma_kernel at 4.06M unknowns, nv = 11); classes without a capture of the
+# current kernel are absent.
+TRAFFIC_RATIO = {"update": 0.983, "project": 1.010}
 
 
 def measured_peaks():

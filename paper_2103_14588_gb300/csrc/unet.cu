@@ -256,6 +256,7 @@ __global__ void dot_kernel(int64_t n, const float *__restrict__ y, const float *
 // Partial sums of <a, r> = sum conj(a_i) r_i (re, im) and ||a||^2 over complex
 // vectors, one triple per CTA (FP64), for the least-squares scale of the correction.
 constexpr int LS_PARTS = 304;
+constexpr int WGRAD_SPLITS = 64;                 // node ranges of the weight-gradient GEMM
 __global__ void __launch_bounds__(256) ls_partials_kernel(int64_t n, const float2 *__restrict__ a,
                                                           const float2 *__restrict__ r, double *__restrict__ part) {
     __shared__ double red[3][256];
@@ -330,6 +331,7 @@ struct dst_unet {
     __nv_bfloat16 *wf[NLAYER], *wt[NLAYER];
     int kpadT[NLAYER];
     float *dw;                                   // largest co x kpad
+    float *dw_part;                              // WGRAD_SPLITS partials of dw
     // activations [N][ch] and their gradients
     float *x0, *a1, *s1, *p1, *a2, *s2, *p2, *a3, *h3, *u2, *q2, *r2, *u1, *q1, *r1, *y;
     float *g_big1, *g_big2, *g_big3, *gs1, *gs2, *g_mid;   // gradient scratch
@@ -409,6 +411,7 @@ static int unet_create(const dst_mesh *mesh, dst_unet **out) {
         maxdw = std::max(maxdw, (size_t)L.co * L.kpad);
     }
     const size_t o_dw = take(sizeof(float) * maxdw);
+    const size_t o_dwp = take(sizeof(float) * maxdw * WGRAD_SPLITS);
     const int64_t acts[] = {N1 * u->C, N1 * 16, N1 * 16, N2 * 16, N2 * 32, N2 * 32, N3 * 32, N3 * 64, N3 * 64,
                             N2 * 64, N2 * 32, N2 * 32, N1 * 32, N1 * 16, N1 * 16, N1 * u->C};
     size_t o_act[16];
@@ -435,6 +438,7 @@ static int unet_create(const dst_mesh *mesh, dst_unet **out) {
         u->wt[l] = (__nv_bfloat16 *)(b + o_wt[l]);
     }
     u->dw = (float *)(b + o_dw);
+    u->dw_part = (float *)(b + o_dwp);
     float **acts_p[16] = {&u->x0, &u->a1, &u->s1, &u->p1, &u->a2, &u->s2, &u->p2, &u->a3, &u->h3,
                           &u->u2, &u->q2, &u->r2, &u->u1, &u->q1, &u->r1, &u->y};
     for (int k = 0; k < 16; ++k) *acts_p[k] = (float *)(b + o_act[k]);
@@ -519,15 +523,17 @@ static int conv_dgrad(dst_unet *u, int l, const float *dz, float *dx, cudaStream
 static int conv_wgrad(dst_unet *u, int l, const float *in, const float *dz, const float *in_scale, cudaStream_t s) {
     const Layer &L = u->L[l];
     const UGrid &g = u->grid[L.level];
-    DST_CUDA_TRY(cudaMemsetAsync(u->dw, 0, sizeof(float) * (size_t)L.co * L.kpad, s));
     WgradArgs a;
     a.g = g; a.ci = L.ci; a.taps = L.taps; a.kpad = L.kpad; a.co = L.co;
-    a.in = in; a.dz = dz; a.in_scale = in_scale; a.dw = u->dw;
-    const int64_t splits = std::min<int64_t>(64, (g.N + 1023) / 1024);
+    a.in = in; a.dz = dz; a.in_scale = in_scale; a.dw = u->dw_part;
+    const int64_t splits = std::min<int64_t>(WGRAD_SPLITS, (g.N + 1023) / 1024);
     a.nodes_per_cta = ((g.N + splits - 1) / splits + 15) / 16 * 16;
     const int ktiles = L.kpad / 8;
     dim3 grid((unsigned)splits, (unsigned)((ktiles + 3) / 4), (unsigned)((L.co + 15) / 16));
+    // every (co < L.co, k < kpad) entry of every split's partial is written by exactly one warp
     conv_wgrad_kernel<<<grid, 128, 0, s>>>(a);
+    const int64_t ndw = (int64_t)L.co * L.kpad;
+    sum_partials_kernel<<<nblk(ndw), 256, 0, s>>>(ndw, (int)splits, u->dw_part, u->dw);
     const int64_t nw = (int64_t)L.co * L.ci * L.taps;
     unpack_wgrad_kernel<<<nblk(nw), 256, 0, s>>>(L, u->dw, u->grads);
     bias_grad_kernel<<<L.co, 256, 0, s>>>(g.N, L.co, dz, u->grads + L.boff);

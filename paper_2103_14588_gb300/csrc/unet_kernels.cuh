@@ -144,12 +144,14 @@ struct WgradArgs {
     const float *in;        // layer input [N][ci]
     const float *dz;        // gradient of the layer's output before its activation [N][co]
     const float *in_scale;  // as in ConvArgs
-    float *dw;              // [co16][kpad] FP32, accumulated with atomics
+    float *dw;              // [splits][co][kpad] FP32: one partial per node range (blockIdx.x)
     int64_t nodes_per_cta;  // node range of one CTA
 };
 
 // dW[co][k] = sum_n dz[n][co] in[n + off(tap(k))][ci(k)]: GEMM with M = co, N = k,
-// K = nodes; one warp per (16 co x 8 k) tile over the CTA's node range.
+// K = nodes; one warp per (16 co x 8 k) tile over the CTA's node range, whose
+// partial goes to its own slice of dw (summed afterwards in a fixed order, so
+// that training is reproducible).
 __global__ void __launch_bounds__(128) conv_wgrad_kernel(WgradArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, tg = lane & 3;
@@ -187,9 +189,19 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(WgradArgs a) {
     // D: (row co = cot*16 + g (+8), col k = ktile*8 + 2 tg + {0, 1})
     const int k0 = ktile * 8 + 2 * tg;
     const int rows[2] = {coA, coB};
+    float *part = a.dw + (size_t)blockIdx.x * a.co * a.kpad;
     for (int h = 0; h < 2; ++h)
         for (int e = 0; e < 2; ++e)
-            if (rows[h] < a.co && k0 + e < a.kpad) atomicAdd(a.dw + (size_t)rows[h] * a.kpad + k0 + e, acc[2 * h + e]);
+            if (rows[h] < a.co && k0 + e < a.kpad) part[(size_t)rows[h] * a.kpad + k0 + e] = acc[2 * h + e];
+}
+
+// dw[i] = sum over the node-range partials, in order
+__global__ void sum_partials_kernel(int64_t n, int splits, const float *__restrict__ part, float *__restrict__ dw) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float t = 0.f;
+    for (int b = 0; b < splits; ++b) t += part[(size_t)b * n + i];
+    dw[i] = t;
 }
 
 }  // namespace dst_nn

@@ -206,3 +206,25 @@ def test_learned_precond_needs_a_matching_network():
         with pytest.raises(B.DstError):
             B.dst_solve(m2.handle, {"mixed_precision": 1, "precond": B.DST_PRECOND_CN_LEARNED}, psi)
         net.close()
+
+
+def test_training_is_reproducible():
+    """Two trainings from the same parameters and seed give the same network bit for bit
+    (the weight gradients sum per node range in a fixed order, no atomics)."""
+    import torch  # noqa: F401
+    from oracle import unet as U
+    from paper_2103_14588_gb300 import binding as B
+    w = W.zb_2p1(n=10, nt=9)
+    om = oracle_mesh(w)
+    flat = _bf16(_flat(U.init_params(w.d, om.nc, seed=9))).astype(np.float32)
+    out = []
+    with B.Mesh.from_workload(w) as mesh:
+        for _ in range(2):
+            net = B.UNet(mesh.handle)
+            net.set_params(flat)
+            losses = net.train(mesh.handle, steps=40, lr=1e-3, seed=21)
+            out.append((losses, net.get_params(), net.output_scale()))
+            net.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
