@@ -389,7 +389,7 @@ constexpr int TMA_CHUNK = 2048;                 // entries per copy (16 KB)
 constexpr int TMA_SLOTS = 6;                    // ring: 6 x 16 KB (two CTAs per SM)
 constexpr int TMA_SMEM = TMA_SLOTS * TMA_CHUNK * 8;
 constexpr unsigned TMA_WAIT_LIMIT = 1u << 22;   // try_wait attempts before a wait is declared failed
-constexpr int TMA_GROUP = 8;                    // basis vectors per pass over a chunk of w
+constexpr int TMA_GROUP = 8;                    // basis vectors per projection CTA (at most)
 
 constexpr int TMA_THREADS = DF_THREADS + 32;   // eight consumer warps and one producer warp
 
