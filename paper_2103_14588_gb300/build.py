@@ -47,7 +47,7 @@ def build(verbose=False):
     with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(_compile, srcs))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), "-shared", ARCH, "-o", tmp] + objs + ["-lpthread"]
+    cmd = [nvcc(), "-shared", ARCH, "-o", tmp] + objs + ["-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

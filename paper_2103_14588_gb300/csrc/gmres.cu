@@ -18,12 +18,20 @@
 // orthogonalisation, Givens rotations and the least-squares update stay FP64.
 // By default a correction is a single GMRES(m) cycle (or less, if it reaches
 // the inner tolerance), so the refinement is restarted GMRES whose restart
-// residual is recomputed with the FP64 operator.
+// residual is recomputed with the FP64 operator; with inner_cycles > 1 the
+// later cycles of a correction restart from the inner residual computed with
+// the FP32 operator.
+//
+// The host marks the phases of a solve with NVTX ranges ("dst_solve", its
+// setup, each GMRES cycle, the FP64 refinement residual, the FP32 inner
+// residual) for timeline tools; without one attached they cost nothing.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <complex>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "blas.h"
 #include "internal.h"
@@ -32,6 +40,14 @@
 namespace {
 
 using cplx = std::complex<double>;
+
+// a named host range for timeline tools (NVTX)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct Workspace {
     int64_t n;
@@ -679,6 +695,7 @@ struct Solver {
     // vlo = false: the basis is stored in FP32 (hi planes only, 8 B per entry)
     // and the same compensated kernels run on it.
     int cycle_df(double2 *d, const double2 *r, int rslot, double rnorm, double tol_abs, int max_iters, bool vlo) {
+        NvtxRange range("GMRES cycle");
         const int m = w.m;
         const int64_t n = w.n;
         const double dn = (double)n;
@@ -857,6 +874,7 @@ extern "C" int dst_default_solve_opts(dst_solve_opts *o) {
 
 static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst_solve_stats &st,
                       cudaStream_t s) {
+    NvtxRange range("dst_solve");
     const bool mixed = o.mixed_precision != 0;
     Solver sv;
     sv.mesh = mesh;
@@ -954,6 +972,7 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
             if (use_df) {
                 rc = sv.cycle_df(sv.w.d, sv.w.r64, 2, rnorm, itol, o.max_iters, o.mixed_ortho == 0);
                 for (int c = 1; rc == DST_OK && c < cycles && sv.resid_est > itol && sv.iters < o.max_iters; ++c) {
+                    NvtxRange ir("inner residual (FP32)");
                     if ((rc = sv.apply(DST_FP32, sv.w.d, sv.w.tmp))) return rc;
                     if ((rc = sv.residual(sv.w.r64, sv.w.tmp, sv.w.rin, sv.w.nrm + 2))) return rc;
                     DST_CUDA_TRY(cudaMemcpyAsync(sv.w.host, sv.w.nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -967,6 +986,7 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
                 rc = sv.gmres(DST_FP32, sv.w.d, sv.w.r64, true, itol, o.max_iters, inner_beta,
                               o.inner_cycles > 0 ? o.inner_cycles : 0x7fffffff);
             if (rc) return rc;
+            NvtxRange rr("refinement residual (FP64)");
             if ((rc = sv.run(K_MISC, 1, 48.0 * n, 2.0 * n, [&] { return dst_k_axpy1(n, sv.w.d, psi, s); }))) return rc;
             if ((rc = sv.apply(DST_FP64, psi, sv.w.tmp))) return rc;
             if ((rc = sv.residual(sv.w.b, sv.w.tmp, sv.w.r64, sv.w.nrm + 2))) return rc;
