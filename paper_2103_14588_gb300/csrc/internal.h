@@ -90,7 +90,6 @@ struct dst_mesh {
     void *d_jac;                  // inverse node blocks of the block Jacobi preconditioner (float2
                                   // [node][NC][NC]), built on first use
     bool jac_valid;               // d_jac matches the current mass and potential
-    int64_t jac_singular;         // nodes whose block was singular (identity used there)
 };
 
 // Node-block Jacobi preconditioner (jacobi.cu): build the inverse blocks of the

@@ -80,10 +80,9 @@ __device__ __forceinline__ double2 cinv(double2 a) {
 
 // inverse of every NC x NC block (NC <= 4), FP64 Gauss-Jordan with partial pivoting,
 // stored in FP32; a block whose pivot vanishes (|pivot| <= 1e-13 of its largest entry)
-// is replaced by the identity and counted in *singular
+// is replaced by the identity (no preconditioning at that node)
 template <int NC>
-__global__ void invert_kernel(int64_t nodes, const double2 *__restrict__ blocks, float2 *__restrict__ binv,
-                              unsigned long long *singular) {
+__global__ void invert_kernel(int64_t nodes, const double2 *__restrict__ blocks, float2 *__restrict__ binv) {
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nodes;
          node += (int64_t)gridDim.x * blockDim.x) {
         double2 a[NC][NC], b[NC][NC];
@@ -134,7 +133,6 @@ __global__ void invert_kernel(int64_t nodes, const double2 *__restrict__ blocks,
                 }
             }
         }
-        if (!ok) atomicAdd(singular, 1ull);
 #pragma unroll
         for (int i = 0; i < NC; ++i)
 #pragma unroll
@@ -202,19 +200,18 @@ int dst_internal_jacobi_setup(dst_mesh *mesh, cudaStream_t s) {
         mesh->d_jac = nullptr;
         return DST_ERR_OOM;
     }
-    // scratch: the probe and its image (FP32 vectors), the FP64 blocks, a counter
+    // scratch: the probe and its image (FP32 vectors), the FP64 blocks
     char *scr = nullptr;
     const size_t vb = ((size_t)n * sizeof(float2) + 255) & ~(size_t)255;
     const size_t bb = ((size_t)nodes * nc * nc * sizeof(double2) + 255) & ~(size_t)255;
-    if (cudaMallocAsync((void **)&scr, 2 * vb + bb + 256, s) != cudaSuccess) {
+    if (cudaMallocAsync((void **)&scr, 2 * vb + bb, s) != cudaSuccess) {
         cudaGetLastError();
         return DST_ERR_OOM;
     }
     float2 *x = reinterpret_cast<float2 *>(scr), *y = reinterpret_cast<float2 *>(scr + vb);
     double2 *blocks = reinterpret_cast<double2 *>(scr + 2 * vb);
-    unsigned long long *singular = reinterpret_cast<unsigned long long *>(scr + 2 * vb + bb);
     const JacGeom g = geometry(mesh);
-    int rc = cudaMemsetAsync(singular, 0, sizeof(unsigned long long), s) == cudaSuccess ? DST_OK : DST_ERR_CUDA;
+    int rc = DST_OK;
     for (int64_t c = 0; c < g.ncolor && rc == DST_OK; ++c)
         for (int comp = 0; comp < nc && rc == DST_OK; ++comp) {
             probe_kernel<<<grid_for(n), 256, 0, s>>>(nodes, nc, g, c, comp, x);
@@ -223,18 +220,14 @@ int dst_internal_jacobi_setup(dst_mesh *mesh, cudaStream_t s) {
         }
     if (rc == DST_OK) {
         float2 *binv = reinterpret_cast<float2 *>(mesh->d_jac);
-        if (nc == 2) invert_kernel<2><<<grid_for(nodes), 128, 0, s>>>(nodes, blocks, binv, singular);
-        else invert_kernel<4><<<grid_for(nodes), 128, 0, s>>>(nodes, blocks, binv, singular);
+        if (nc == 2) invert_kernel<2><<<grid_for(nodes), 128, 0, s>>>(nodes, blocks, binv);
+        else invert_kernel<4><<<grid_for(nodes), 128, 0, s>>>(nodes, blocks, binv);
     }
-    unsigned long long nsing = 0;
-    if (rc == DST_OK && (cudaGetLastError() != cudaSuccess ||
-                         cudaMemcpyAsync(&nsing, singular, sizeof(nsing), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                         cudaStreamSynchronize(s) != cudaSuccess))
+    if (rc == DST_OK && (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess))
         rc = DST_ERR_CUDA;
     cudaFreeAsync(scr, s);
     if (rc != DST_OK) return rc;
     mesh->jac_valid = true;
-    mesh->jac_singular = (int64_t)nsing;
     return DST_OK;
 }
 

@@ -252,7 +252,6 @@ extern "C" int dst_create_mesh(int d, const int64_t n_el[4], const double lo[4],
     m->unet = nullptr;
     m->d_jac = nullptr;
     m->jac_valid = false;
-    m->jac_singular = 0;
     m->ws = nullptr;
     m->host_pinned = nullptr;
     m->tile_variant[0] = m->tile_variant[1] = 0;
