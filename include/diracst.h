@@ -223,7 +223,7 @@ typedef struct {
                                exact FP32 products and compensated sums: inner products of the
                                stored values err by about 2^-40 of ||v|| ||w||, updates are
                                rounded to FP32 once, each new basis vector is rounded to
-                               FP32 once; from 4M unknowns the projection is fed by bulk
+                               FP32 once; from 1M unknowns the projection and the update are fed by bulk
                                asynchronous copies */
     int method;             /* Krylov method: 0 = restarted GMRES(restart) (default),
                                1 = BiCGSTAB (van der Vorst 1992; FP64 only, mixed_precision
@@ -370,7 +370,7 @@ DST_API int dst_observables(const dst_mesh *mesh, const void *psi, double x0, vo
  *                        has in flight, flags the step, and dst_solve returns
  *                        DST_ERR_CUDA naming the wait in dst_last_error_detail().
  *                        Only mixed solves on an FP32-stored basis of at least
- *                        4,000,000 unknowns use that kernel.
+ *                        1,000,000 unknowns use those kernels.
  *   DST_TEST_FAIL_ALLOC  value = how many of the following GMRES workspace
  *                        allocations fail as if the device were out of memory
  *                        (dst_solve returns DST_ERR_OOM, the mesh stays usable);

@@ -7,8 +7,8 @@ Nothing here faults, traps or hangs the GPU:
   kernel stops consuming, waits with the standard limit for the copies it has
   in flight, and flags the step.  The solve must return DST_ERR_CUDA naming
   the wait, and the same mesh must solve normally once the limit is restored.
-  The kernel serves mixed solves on an FP32-stored basis from 4,000,000
-  unknowns: the 3+1 Klein workload at 32^3 x 32 (4,063,232) is the case.
+  The bulk-copy fed kernels serve mixed solves on an FP32-stored basis from
+  1,000,000 unknowns: the 3+1 Klein workload at 32^3 x 32 (4,063,232) is the case.
 * A workspace allocation that fails: DST_ERR_OOM, then a normal solve.
 """
 import numpy as np
@@ -24,7 +24,7 @@ def test_bulk_copy_wait_timeout_reports_cuda_error():
     from paper_2103_14588_gb300 import binding as B
     w = W.klein_3p1(n=32, nt=32, p0=1.05)
     with B.Mesh.from_workload(w) as mesh:
-        assert mesh.n_unknowns >= 4000000
+        assert mesh.n_unknowns >= 1000000
         psi = torch.zeros(mesh.n_unknowns, dtype=torch.complex128, device="cuda")
         opts = {"restart": 30, "rtol": 1e-8, "max_iters": 30, "mixed_precision": 1}
         B.dst_testing_set(B.DST_TEST_WAIT_LIMIT, 0)

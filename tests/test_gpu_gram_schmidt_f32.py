@@ -10,8 +10,8 @@ FP32's 2^-24 per term, short of FP64).  Checked here at 2^-36 ||v_j|| ||w||
 (a regression that lost ten bits fails) against an FP64 evaluation of the same
 stored values (each product of two FP32 numbers is exact in FP64; the FP64 sums
 err by ~n 2^-53 of sum |v| |w|, far below the bound), for the register-fed and
-the bulk-copy fed projection, at a size below and one above the
-4,000,000-entry switch between them.  The update: the result is w - V h
+the bulk-copy fed projection, at sizes on both sides of the 1,000,000-entry
+switch between them in the solver (each kernel is called directly at every size).  The update: the result is w - V h
 rounded to FP32 once, so it is checked at half an FP32 ulp of the exact value
 plus 2^-36 of the anchor scale (max |w component| + sum_j |h_j|_1).
 """
@@ -77,7 +77,7 @@ def test_update_error_bound(n, nvec):
 
 @pytest.mark.parametrize("n,nvec", [(4063232, 9), (6 * 2048 + 2, 3), (4063232, 30)])
 def test_bulk_copy_update_equals_register_update(n, nvec):
-    """The update fed by bulk copies (mode 3, the solver's from 4M unknowns) does the
+    """The update fed by bulk copies (mode 3, the solver's from 1M unknowns) does the
     register-fed update's arithmetic per entry: the same stored w bit for bit, and
     the same ||w||^2 up to the order of the FP64 partial sums."""
     import torch
