@@ -389,10 +389,13 @@ DST_API int dst_testing_set(int hook, int64_t value);
  *   mode 1: the same by the bulk-copy fed projection;
  *   mode 2: w <- w - V h (h: DEVICE FP64 complex input), rounded to FP32 once,
  *           and *nrm2 (DEVICE double) = ||w||^2 of the stored result;
- *   mode 3: the same update with the basis fed by bulk copies.
+ *   mode 3: the same update with the basis fed by bulk copies;
+ *   mode 4: x <- x + V y with x = w read as a DEVICE FP64 complex vector of n
+ *           entries and y = h (the end-of-cycle correction; nrm2 unused);
+ *   mode 5: the same with the basis fed by bulk copies.
  * Products are exact and sums compensated: the error of h_j is about 2^-40 of
  * ||v_j|| ||w|| (measured with unit basis vectors).  Takes stream-ordered
- * scratch; modes 1 and 3 synchronise the stream.  Errors: DST_ERR_ARG, DST_ERR_OOM,
+ * scratch; modes 1, 3 and 5 synchronise the stream.  Errors: DST_ERR_ARG, DST_ERR_OOM,
  * DST_ERR_CUDA (a bulk-copy wait that gave up).
  */
 DST_API int dst_testing_fp32_arnoldi(int mode, int64_t n, int nvec, const void *V, void *w, void *h, void *nrm2,

@@ -52,6 +52,10 @@ int dst_k_project_tma(int64_t n, int nvec, const float2 *V, const float2 *w, dou
 int dst_k_update_tma(int64_t n, int nvec, const float2 *V, const double2 *h, float2 *w, double *nrm2,
                      double *partials, int nblk, cudaStream_t s, const double *gate, double *counter,
                      unsigned *ticket, double *err);
+// x += V y (FP32-stored basis, k vectors) with the basis fed by the same bulk copies;
+// the per-entry arithmetic of dst_k_combine_df.  A failed wait sets *err = 1.
+int dst_k_combine_tma(int64_t n, int k, const float2 *V, const double2 *y, double2 *x, int nblk, cudaStream_t s,
+                      double *err);
 int dst_k_split_f64_df(int64_t n, const double2 *src, const double *nrm2, float2 *dst, cudaStream_t s,
                        bool vlo = true);
 int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double2 *x, cudaStream_t s,

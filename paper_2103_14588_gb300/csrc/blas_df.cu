@@ -792,6 +792,135 @@ update_tma_kernel(int64_t n, int nvec, const float2 *__restrict__ V, const doubl
     }
 }
 
+// x (FP64) <- x + sum_j V_j y_j at the end of a cycle, with the FP32-stored
+// basis streamed through the bulk-copy ring of project_tma_kernel: per chunk of
+// the CTA's slice the consumers accumulate every vector's chunk as it lands, in
+// the arithmetic of combine_df_kernel<false> per entry (df32 sum over the
+// vectors in order, one conversion; bit for bit the same), then read, update
+// and store the chunk of x.  Same failure handling as project_tma_kernel
+// (*err = 1; the chunks not reached keep their old x).
+__global__ void __launch_bounds__(TMA_THREADS, 2)
+combine_tma_kernel(int64_t n, int k, const float2 *__restrict__ V, const double2 *__restrict__ y,
+                   double2 *__restrict__ x, double *err, unsigned wait_limit) {
+    constexpr int NW = DF_THREADS / 32;
+    constexpr int U = TMA_CHUNK / 2;
+    constexpr int UPT = U / DF_THREADS;
+    extern __shared__ __align__(128) float4 ring[];
+    __shared__ __align__(8) uint64_t full[TMA_SLOTS], empty[TMA_SLOTS];
+    __shared__ float4 ys[DST_MAX_VEC];              // -y split: (re_hi, re_lo, im_hi, im_lo)
+    __shared__ int failed, s_issued, s_done[NW];
+    volatile int *vfailed = &failed;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int64_t b, e;
+    df_slice2(n, b, e);
+    const int64_t len = e > b ? e - b : 0;
+    const int nch = (int)((len + TMA_CHUNK - 1) / TMA_CHUNK);
+    const int K = nch * k;
+    for (int j = tid; j < k; j += TMA_THREADS) {
+        const double2 c = y[j];
+        const float rh = (float)(-c.x), ih = (float)(-c.y);
+        ys[j] = make_float4(rh, (float)(-c.x - (double)rh), ih, (float)(-c.y - (double)ih));
+    }
+    if (tid == 0) {
+        for (int q = 0; q < TMA_SLOTS; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], NW);
+        }
+        failed = 0;
+        s_issued = 0;
+        for (int q = 0; q < NW; ++q) s_done[q] = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == NW) {
+        if (lane == 0) {
+            int pc = 0, pq = 0, kk = 0;
+            for (; kk < K && !*vfailed; ++kk) {
+                const int slot = kk % TMA_SLOTS;
+                if (kk >= TMA_SLOTS &&
+                    !mbar_wait_bounded(&empty[slot], (unsigned)(((kk / TMA_SLOTS) - 1) & 1), wait_limit)) {
+                    *vfailed = 1;
+                    break;
+                }
+                const int64_t c0 = b + (int64_t)pc * TMA_CHUNK;
+                const int64_t cnt = e - c0 < TMA_CHUNK ? e - c0 : TMA_CHUNK;
+                const unsigned bytes = (unsigned)(cnt * (int64_t)sizeof(float2));
+                mbar_arrive_expect_tx(&full[slot], bytes);
+                bulk_g2s(ring + (size_t)slot * U, V + (int64_t)pq * n + c0, bytes, &full[slot]);
+                if (++pq == k) { pq = 0; ++pc; }
+            }
+            s_issued = kk;
+        }
+    } else {
+        int q = 0;                                   // copies this warp waited for (and released)
+        auto wait_item = [&]() -> const float4 * {
+            const int slot = q % TMA_SLOTS;
+            bool ok = __shfl_sync(0xffffffffu, *vfailed == 0 ? 1 : 0, 0) != 0;
+            if (ok) ok = mbar_wait_bounded(&full[slot], (unsigned)((q / TMA_SLOTS) & 1), wait_limit);
+            ok = __all_sync(0xffffffffu, ok) != 0;
+            if (!ok) {
+                if (lane == 0) *vfailed = 1;
+                return nullptr;
+            }
+            return (const float4 *)(ring + (size_t)slot * U);
+        };
+        auto release_item = [&]() {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[q % TMA_SLOTS]);
+            ++q;
+        };
+        bool stop = false;
+        for (int c = 0; c < nch && !stop; ++c) {
+            const int64_t c0 = b + (int64_t)c * TMA_CHUNK;
+            const int units = (int)(((e - c0 < TMA_CHUNK) ? e - c0 : TMA_CHUNK) >> 1);
+            DfAcc ar[UPT][2], ai[UPT][2];
+#pragma unroll
+            for (int i = 0; i < UPT; ++i)
+#pragma unroll
+                for (int t = 0; t < 2; ++t) { ar[i][t].zero(); ai[i][t].zero(); }
+            for (int j = 0; j < k; ++j) {
+                const float4 *sv = wait_item();
+                if (!sv) { stop = true; break; }
+                const float4 cj = ys[j];
+#pragma unroll
+                for (int i = 0; i < UPT; ++i) {
+                    const int u = tid + i * DF_THREADS;
+                    if (u < units) {
+                        const float4 v = sv[u];
+                        caxpy_sub<false>(v.x, v.y, 0.f, 0.f, cj, ar[i][0], ai[i][0]);
+                        caxpy_sub<false>(v.z, v.w, 0.f, 0.f, cj, ar[i][1], ai[i][1]);
+                    }
+                }
+                release_item();
+            }
+            if (stop) break;
+#pragma unroll
+            for (int i = 0; i < UPT; ++i) {
+                const int u = tid + i * DF_THREADS;
+                if (u >= units) continue;
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int64_t idx = c0 + 2 * (int64_t)u + t;
+                    double2 acc = x[idx];
+                    acc.x += ar[i][t].value();
+                    acc.y += ai[i][t].value();
+                    x[idx] = acc;
+                }
+            }
+        }
+        if (lane == 0) s_done[warp] = q;
+    }
+    __syncthreads();
+    if (tid == 0 && *vfailed) {
+        int lo = s_done[0];
+        for (int w = 1; w < NW; ++w) lo = s_done[w] < lo ? s_done[w] : lo;
+        for (int w = lo; w < s_issued; ++w)
+            mbar_wait_bounded(&full[w % TMA_SLOTS], (unsigned)((w / TMA_SLOTS) & 1), TMA_WAIT_LIMIT);
+        if (err) *err = 1.0;
+    }
+    __syncthreads();
+}
+
 // w <- w - sum_j V_j h_j for an FP32-stored unit-norm basis and FP32 w (h in
 // FP64, split per CTA), rounded to FP32 once; partials of ||w||^2 of the
 // stored result.  Per entry the bound is |w component| + sum_j |h_j|_1.
@@ -1086,6 +1215,23 @@ int dst_k_update_tma(int64_t n, int nvec, const float2 *V, const double2 *h, flo
     return DST_OK;
 }
 
+int dst_k_combine_tma(int64_t n, int k, const float2 *V, const double2 *y, double2 *x, int nblk, cudaStream_t s,
+                      double *err) {
+    if (n & 1) return DST_ERR_ARG;
+    if (k < 1) return DST_OK;
+    static bool configured[64] = {};
+    int dev = 0;
+    DST_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        DST_CUDA_TRY(cudaFuncSetAttribute(combine_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM));
+        if (dev >= 0 && dev < 64) configured[dev] = true;
+    }
+    combine_tma_kernel<<<nblk, TMA_THREADS, TMA_SMEM, s>>>(n, k, V, y, x, err,
+                                                           dst_internal_wait_limit(TMA_WAIT_LIMIT));
+    DST_CUDA_TRY(cudaGetLastError());
+    return DST_OK;
+}
+
 int dst_k_update_df(int64_t n, int nvec, const float2 *V, const double2 *h, float2 *w, bool w_hi_only, double *nrm2,
                     double *partials, int nblk, cudaStream_t s, const double *gate, double *counter,
                     unsigned *ticket, bool vlo) {
@@ -1133,16 +1279,16 @@ int dst_k_combine_df(int64_t n, int k, const float2 *V, const double2 *y, double
 
 extern "C" int dst_testing_fp32_arnoldi(int mode, int64_t n, int nvec, const void *V, void *w, void *h, void *nrm2,
                                         void *stream) {
-    if (mode < 0 || mode > 3 || n < 2 || (n & 1) || nvec < 1 || nvec > DST_MAX_VEC || !V || !w || !h ||
-        (mode >= 2 && !nrm2)) {
+    if (mode < 0 || mode > 5 || n < 2 || (n & 1) || nvec < 1 || nvec > DST_MAX_VEC || !V || !w || !h ||
+        ((mode == 2 || mode == 3) && !nrm2)) {
         dst_internal_set_error_detail("dst_testing_fp32_arnoldi: bad mode, size (n even >= 2, 1 <= nvec <= 64) "
                                       "or pointer");
         return DST_ERR_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int nblk_reg = std::min(dst_reduction_blocks(n), 3 * 152);
-    const int nblk = (mode == 1 || mode == 3) ? dst_tma_projection_blocks(n)
-                                              : (mode == 2 ? dst_reduction_blocks(n) : nblk_reg);
+    const int nblk = (mode == 1 || mode == 3 || mode == 5) ? dst_tma_projection_blocks(n)
+                                                            : (mode == 2 ? dst_reduction_blocks(n) : nblk_reg);
     const size_t pbytes = sizeof(double2) * (size_t)nblk * (nvec + 1);
     char *scr = nullptr;
     if (cudaMallocAsync((void **)&scr, pbytes + 256 + 256, s) != cudaSuccess) {
@@ -1164,12 +1310,16 @@ extern "C" int dst_testing_fp32_arnoldi(int mode, int64_t n, int nvec, const voi
         else if (mode == 2)
             rc = dst_k_update_df(n, nvec, (const float2 *)V, (const double2 *)h, (float2 *)w, true, (double *)nrm2,
                                  (double *)partials, nblk, s, nullptr, nullptr, ticket + 1, false);
-        else
+        else if (mode == 3)
             rc = dst_k_update_tma(n, nvec, (const float2 *)V, (const double2 *)h, (float2 *)w, (double *)nrm2,
                                   (double *)partials, nblk, s, nullptr, nullptr, ticket + 1, err);
+        else if (mode == 4)
+            rc = dst_k_combine_df(n, nvec, (const float2 *)V, (const double2 *)h, (double2 *)w, s, false);
+        else
+            rc = dst_k_combine_tma(n, nvec, (const float2 *)V, (const double2 *)h, (double2 *)w, nblk, s, err);
     }
     double e = 0.0;
-    if (rc == DST_OK && (mode == 1 || mode == 3) &&
+    if (rc == DST_OK && (mode == 1 || mode == 3 || mode == 5) &&
         (cudaMemcpyAsync(&e, err, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
          cudaStreamSynchronize(s) != cudaSuccess))
         rc = DST_ERR_CUDA;

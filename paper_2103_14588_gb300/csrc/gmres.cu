@@ -741,8 +741,12 @@ struct Solver {
         hs.solve(k, w.host, 1.0);
         DST_CUDA_TRY(cudaMemcpyAsync(w.h1, w.host, sizeof(double2) * k, cudaMemcpyHostToDevice, s));
         const float2 *basis = precond ? w.Z : Vd;       // flexible GMRES: d = Z y
-        if ((rc = run(K_UPDATE, 1, vb * dn * k + 32.0 * dn, 8.0 * dn * k,
-                      [&] { return dst_k_combine_df(n, k, basis, w.h1, d, s, vlo); })))
+        // large FP32-stored bases: the basis fed by bulk copies; a failed wait flags nrm[7]
+        const bool tma = !vlo && n >= TMA_MIN_UNKNOWNS;
+        if ((rc = run(K_UPDATE, 1, vb * dn * k + 32.0 * dn, 8.0 * dn * k, [&] {
+                 return tma ? dst_k_combine_tma(n, k, basis, w.h1, d, dst_tma_projection_blocks(n), s, w.nrm + 7)
+                            : dst_k_combine_df(n, k, basis, w.h1, d, s, vlo);
+             })))
             return rc;
         ++restarts;
         return DST_OK;
@@ -918,7 +922,7 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
     const int64_t n = mesh->n_unknowns;
     // b = -D_w21 psi0 and ||b||
     sv.prof.on = o.profile != 0;
-    DST_CUDA_TRY(cudaMemsetAsync(sv.w.nrm, 0, 8 * sizeof(double), s));
+    DST_CUDA_TRY(cudaMemsetAsync(sv.w.nrm, 0, 8 * sizeof(double), s));      // nrm[7]: the combine's failed-wait flag
     DST_CUDA_TRY(cudaMemsetAsync(sv.w.tickets, 0, 8 * sizeof(unsigned), s));
     if ((rc = sv.run(K_RHS, 1, 16.0 * n + 16.0 * mesh->n_spatial * mesh->nc, 0.0,
                      [&] { return dst_internal_rhs(mesh, sv.w.b, s); })))
@@ -999,7 +1003,12 @@ static int solve_impl(dst_mesh *mesh, const dst_solve_opts &o, double2 *psi, dst
         st.refinements = refine;
         beta = rnorm;
     }
+    DST_CUDA_TRY(cudaMemcpyAsync(sv.w.host + 1, sv.w.nrm + 7, sizeof(double), cudaMemcpyDeviceToHost, s));
     if ((rc = sv.sync())) return rc;
+    if (sv.w.host[1] != 0.0) {
+        dst_internal_set_error_detail("dst_solve: a bulk-copy wait of the end-of-cycle combine timed out");
+        return DST_ERR_CUDA;
+    }
     for (int c = 0; c < K_NCLASS; ++c) {
         st.kernel_ms[c] = sv.prof.ms[c];
         st.kernel_launches[c] = sv.prof.launches[c];

@@ -97,3 +97,25 @@ def test_bulk_copy_update_equals_register_update(n, nvec):
     torch.cuda.synchronize()
     assert torch.equal(w_tma, w_reg)
     assert abs(float(n_tma[0]) - float(n_reg[0])) <= 1e-13 * float(n_reg[0])
+
+
+@pytest.mark.parametrize("n,nvec", [(4063232, 30), (6 * 2048 + 2, 3), (1769472, 17)])
+def test_bulk_copy_combine_equals_register_combine(n, nvec):
+    """x += V y at the end of a cycle, fed by bulk copies (mode 5, the solver's from 1M
+    unknowns) against the register-fed combine (mode 4): the same FP64 x bit for bit."""
+    import torch
+    from paper_2103_14588_gb300 import binding as B
+    lib = B.library()
+    gen = torch.Generator(device="cuda").manual_seed(11 * n + nvec)
+    V = torch.randn(nvec, n, dtype=torch.complex128, device="cuda", generator=gen)
+    V = (V / torch.linalg.vector_norm(V, dim=1, keepdim=True)).to(torch.complex64).contiguous()
+    x = torch.randn(n, dtype=torch.complex128, device="cuda", generator=gen)
+    y = torch.randn(nvec, dtype=torch.complex128, device="cuda", generator=gen)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    x_reg, x_tma = x.clone(), x.clone()
+    assert lib.dst_testing_fp32_arnoldi(4, n, nvec, _ptr(V), _ptr(x_reg), _ptr(y), None, st) == 0
+    assert lib.dst_testing_fp32_arnoldi(5, n, nvec, _ptr(V), _ptr(x_tma), _ptr(y), None, st) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(x_tma, x_reg)
+    ref = x + (y[:, None] * V.to(torch.complex128)).sum(dim=0)
+    assert (x_reg - ref).abs().max().item() <= 1e-12 * ref.abs().max().item()
